@@ -1,0 +1,177 @@
+"""Seeded synthetic inputs for the RNSM merge path.
+
+This module is shared by the FP64 oracle's tests and by the CUDA path's tests
+and benchmark.  It holds random-number recipes only: no distance, search,
+prune or ordering arithmetic of the merge method lives here.
+
+The paper measures on SIFT, DEEP, GIST, IMAGE, ANTON and MARCO (Section 6,
+Table "Dataset Statistics").  None of those datasets is available, so every
+workload below is a seeded stand-in with the same dimension, scale, value
+distribution and partition type (random vs cluster partitions, Section 3.1).
+
+Workloads (sizes are parameters so the same recipe serves small parity cases):
+
+* ``gaussian``      -- iid N(0,1) rows (the tiny parity case, d=32).
+* ``sift_like``     -- 1,000-component Gaussian mixture rounded and clipped to
+                       integers 0..255, d=128 (SIFT stand-in).  Every value is
+                       an integer, so squared-L2 distances are exact in FP32.
+* ``deep_like``     -- unit-norm d=96 mixture (DEEP stand-in).
+* ``embed_like``    -- unit-norm d=768 mixture of anisotropic Gaussians
+                       (IMAGE embedding stand-in, inner product).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+__all__ = [
+    "gaussian",
+    "sift_like",
+    "deep_like",
+    "embed_like",
+    "random_partition",
+    "cluster_partition",
+    "lognormal_sizes",
+    "tiny_case",
+    "sift_case",
+]
+
+
+def _rng(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def gaussian(n: int, d: int, seed: int) -> np.ndarray:
+    """iid N(0,1) rows, float32, shape [n, d]."""
+    return _rng(seed).standard_normal((n, d), dtype=np.float64).astype(np.float32)
+
+
+def _sift_mixture(seed: int, d: int, n_comp: int):
+    g = _rng(seed)
+    centers = g.uniform(0.0, 128.0, size=(n_comp, d))
+    sigma = g.uniform(10.0, 30.0, size=n_comp)
+    return g, centers, sigma
+
+
+def sift_like(n: int, seed: int, d: int = 128, n_comp: int = 1000,
+              chunk: int = 1 << 18) -> np.ndarray:
+    """Integer-valued Gaussian mixture: centers U[0,128]^d, sigma_j ~ U[10,30],
+    x = clip(round(center + sigma * N(0,1)), 0, 255), uniform weights."""
+    g, centers, sigma = _sift_mixture(seed, d, n_comp)
+    out = np.empty((n, d), dtype=np.float32)
+    for s in range(0, n, chunk):
+        e = min(n, s + chunk)
+        comp = g.integers(0, n_comp, size=e - s)
+        z = g.standard_normal((e - s, d))
+        x = centers[comp] + sigma[comp, None] * z
+        out[s:e] = np.clip(np.rint(x), 0.0, 255.0).astype(np.float32)
+    return out
+
+
+def _normalise(x: np.ndarray) -> np.ndarray:
+    nrm = np.sqrt(np.einsum("ij,ij->i", x, x))
+    nrm[nrm == 0.0] = 1.0
+    return x / nrm[:, None]
+
+
+def deep_like(n: int, seed: int, d: int = 96, n_comp: int = 1000,
+              sigma: float = 0.35, return_components: bool = False,
+              chunk: int = 1 << 18):
+    """Unit-norm mixture: means N(0,I) normalised, isotropic sigma, renormalised.
+
+    With ``return_components`` the component index of each row and the
+    component means are returned too (used by the cluster partition)."""
+    g = _rng(seed)
+    means = _normalise(g.standard_normal((n_comp, d)))
+    comp_all = g.integers(0, n_comp, size=n)
+    out = np.empty((n, d), dtype=np.float32)
+    for s in range(0, n, chunk):
+        e = min(n, s + chunk)
+        comp = comp_all[s:e]
+        x = means[comp] + sigma * g.standard_normal((e - s, d))
+        out[s:e] = _normalise(x).astype(np.float32)
+    if return_components:
+        return out, comp_all, means
+    return out
+
+
+def embed_like(n: int, seed: int, d: int = 768, n_comp: int = 2000,
+               rank: int = 32, noise: float = 0.02, chunk: int = 1 << 15) -> np.ndarray:
+    """Unit-norm anisotropic mixture: x = normalise(mu_j + A_j z + noise*eps),
+    A_j a d x rank matrix with singular values 0.3 * 0.9^i, z ~ N(0, I_rank)."""
+    g = _rng(seed)
+    means = _normalise(g.standard_normal((n_comp, d)))
+    sv = 0.3 * (0.9 ** np.arange(rank))
+    # Orthonormal-ish column bases per component: Gaussian columns normalised.
+    basis = g.standard_normal((n_comp, d, rank)).astype(np.float32)
+    basis /= np.sqrt((basis.astype(np.float64) ** 2).sum(axis=1, keepdims=True)).astype(np.float32)
+    basis *= sv[None, None, :].astype(np.float32)
+    comp_all = g.integers(0, n_comp, size=n)
+    out = np.empty((n, d), dtype=np.float32)
+    for s in range(0, n, chunk):
+        e = min(n, s + chunk)
+        comp = comp_all[s:e]
+        z = g.standard_normal((e - s, rank)).astype(np.float32)
+        x = means[comp] + np.einsum("bdr,br->bd", basis[comp], z) \
+            + noise * g.standard_normal((e - s, d))
+        out[s:e] = _normalise(x).astype(np.float32)
+    return out
+
+
+def random_partition(n: int, m: int, seed: int) -> list[np.ndarray]:
+    """Equal-size random split of row indices 0..n-1 into m parts (Section 3.1)."""
+    perm = _rng(seed).permutation(n)
+    return [np.sort(p) for p in np.array_split(perm, m)]
+
+
+def lognormal_sizes(m: int, total: int, lo: int, hi: int, seed: int,
+                    sigma: float = 0.6) -> np.ndarray:
+    """m segment sizes ~ lognormal(sigma), rescaled to ``total``, clipped to [lo, hi]."""
+    g = _rng(seed)
+    w = g.lognormal(0.0, sigma, size=m)
+    sizes = np.clip(np.rint(w / w.sum() * total), lo, hi).astype(np.int64)
+    # Spread the rounding/clipping remainder over unclipped segments.
+    diff = int(total - sizes.sum())
+    i = 0
+    while diff != 0 and i < 100 * m:
+        j = i % m
+        step = 1 if diff > 0 else -1
+        if lo <= sizes[j] + step <= hi:
+            sizes[j] += step
+            diff -= step
+        i += 1
+    return sizes
+
+
+def cluster_partition(comp: np.ndarray, means: np.ndarray, sizes: np.ndarray,
+                      seed: int) -> list[np.ndarray]:
+    """Cluster partition: components sorted by a random projection of their
+    means, their rows assigned contiguously to fill each segment in turn."""
+    g = _rng(seed)
+    proj = means @ g.standard_normal(means.shape[1])
+    comp_rank = np.empty(len(means), dtype=np.int64)
+    comp_rank[np.argsort(proj, kind="stable")] = np.arange(len(means))
+    order = np.lexsort((np.arange(len(comp)), comp_rank[comp]))
+    bounds = np.concatenate([[0], np.cumsum(sizes)])
+    return [np.sort(order[bounds[i]:bounds[i + 1]]) for i in range(len(sizes))]
+
+
+def tiny_case(n_per_seg: int = 5000, d: int = 32, seed_data: int = 1, seed_query: int = 2,
+              nq: int = 1000):
+    """2 x n_per_seg iid N(0,1) rows; segment 0 = first half, segment 1 = second half."""
+    X = gaussian(2 * n_per_seg, d, seed_data)
+    Q = gaussian(nq, d, seed_query)
+    return [X[:n_per_seg].copy(), X[n_per_seg:].copy()], Q
+
+
+def sift_case(n_per_seg: int = 500_000, m: int = 2, seed_data: int = 3, seed_query: int = 4,
+              nq: int = 10_000, d: int = 128):
+    """SIFT-like integer mixture, random partition into m equal segments.
+
+    The queries come from the same mixture (same centers and sigmas)."""
+    n = n_per_seg * m
+    X = sift_like(n + nq, seed_data, d=d)
+    Q = X[n:].copy()
+    X = X[:n]
+    parts = random_partition(n, m, seed_data + 1000)
+    del seed_query  # queries share the mixture draw above
+    return [X[p].copy() for p in parts], Q
