@@ -814,7 +814,7 @@ int32_t orc_rnsm_merge(const float *X, int64_t d, const int64_t *seg_off, int32_
                        const int32_t *plan_dst, int32_t n_plan, int32_t *out_adj, int64_t *stats,
                        int32_t nthreads) {
     if (m < 1 || R < 1 || L < 1 || r_in < 0 || r_in > R || k_rev < 1 || k_plus < k_rev ||
-        ef_slide < 1 || c_cross < 1 || c_cross > L || c_cross > ef_slide)
+        ef_slide < 1 || ef_slide > L || c_cross < 1 || c_cross > ef_slide)
         return ORC_EINVAL;
     set_threads(nthreads);
     int64_t N = seg_off[m];

@@ -1,0 +1,119 @@
+// Internal launchers shared by the translation units of librnsm.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace rnsm {
+
+enum SeedMode : int32_t { kSeedConst = 0, kSeedSelf = 1, kSeedTable = 2 };
+
+// One batched beam-search launch (Algorithm 1).  Query i reads
+// qvecs[qrow * dim] with qrow = qidx ? qidx[i] : i.
+struct SearchArgs {
+    const float *base;      // searched vector set [n_base * dim]
+    int64_t n_base;
+    const int32_t *adj;     // [n_base * r_in]
+    int32_t r_in;
+    int32_t dim;
+    int32_t metric;
+    const float *qvecs;
+    const int32_t *qidx;    // nullable
+    int64_t nq;
+    int32_t seed_mode;      // SeedMode
+    int32_t seed_const;     // kSeedConst: the single entry vertex
+    const int32_t *seed_tab;  // kSeedTable: rows of seeds
+    int32_t seed_stride;
+    int32_t n_seeds;
+    const int32_t *seed_row;  // kSeedTable: row = seed_row ? seed_row[qrow] : i
+    int32_t ef;
+    int32_t k;
+    int32_t exclude_self;     // drop result id == qrow (neighbour expansion)
+    int32_t *out_ids;         // row = out_by_qidx ? qrow : i
+    int32_t out_stride;
+    int32_t out_by_qidx;
+    int32_t id_offset;        // added to every written id
+    float *out_d;             // nullable, same layout as out_ids
+    int64_t *out_ndc;         // nullable, [nq]
+    unsigned long long *stats;  // nullable: [0] += NDC, [1] += expansions
+    int32_t *work;            // zeroed work counter
+};
+
+cudaError_t launch_search(const SearchArgs &a, cudaStream_t st);
+
+// Occlusion prune (UpdateGraph) of a batch of owners over a segment table.
+// Owner i is global id owner_ids ? owner_ids[i] : owner_base + i.  Its pool
+// is the union of: listA row gid (lenA ids), listB row i (lenB ids, offB
+// added to non-negative ones), CSR row i (csr_offs/csr_ids).
+struct PruneArgs {
+    SegTable segs;
+    int32_t dim;
+    int32_t metric;
+    float alpha;
+    int32_t R;
+    int32_t keep_all_if_fit;
+    int32_t skip_empty_csr;   // owners with no CSR entries are left untouched
+    int64_t n_owners;
+    const int32_t *owner_ids;
+    int32_t owner_base;
+    const int32_t *listA;
+    int32_t lenA;
+    const int32_t *listB;
+    int32_t strideB;
+    int32_t lenB;
+    int32_t offB;
+    const int64_t *csr_offs;
+    const int32_t *csr_ids;
+    int32_t csr_max;          // longest CSR row (sizes the pool buffer)
+    int32_t *out;             // rows by owner gid (out_by_index: by i), stride R
+    int32_t out_by_index;
+    int32_t emit_lo, emit_hi; // kept ids in [emit_lo, emit_hi) emit (u, owner)
+    int32_t *eu;
+    int32_t *ev;
+    unsigned long long *ecount;
+    int32_t *work;
+    int32_t *err;             // bit 4: pool larger than the capacity
+};
+
+cudaError_t launch_prune(const PruneArgs &a, cudaStream_t st);
+
+// Counting sort of (key, val) pairs by key into CSR (K3).
+// keys/vals [cap], the number of valid pairs at *count (device) or n_host.
+cudaError_t launch_bucket(const int32_t *keys, const int32_t *vals, int64_t cap,
+                          const unsigned long long *count, int64_t nkeys, int32_t key_offset,
+                          int64_t *offs /*[nkeys+1]*/, int32_t *cursor /*[nkeys]*/,
+                          int32_t *out_vals, void *scan_tmp, size_t scan_tmp_bytes,
+                          cudaStream_t st);
+size_t bucket_scan_tmp_bytes(int64_t nkeys);
+
+// Sorts every CSR row ascending (rows of at most 4096 entries).
+cudaError_t launch_sort_rows(const int64_t *offs, int32_t *ids, int64_t nrows, int32_t *err,
+                             cudaStream_t st);
+
+// (N+ first k columns) -> pairs (x, y) for the reverse-kNN inversion.
+cudaError_t launch_rk_pairs(const int32_t *nplus, int64_t n, int32_t k_plus, int32_t k,
+                            int32_t *keys, int32_t *vals, unsigned long long *count,
+                            cudaStream_t st);
+
+// *out = longest row of a CSR with n rows.
+cudaError_t launch_max_row(const int64_t *offs, int64_t n, int32_t *out, cudaStream_t st);
+
+bool search_dim_supported(int dim);
+
+cudaError_t launch_validate_graph(const int32_t *adj, int64_t n, int32_t r_in, int32_t *err,
+                                  cudaStream_t st);
+// Sets bit 1 of *err if an id is outside [allow_minus1 ? -1 : 0, bound).
+cudaError_t launch_validate_ids(const int32_t *ids, int64_t count, int64_t bound,
+                                int32_t allow_minus1, int32_t *err, cudaStream_t st);
+cudaError_t launch_validate_vecs(const float *v, int64_t count, int32_t *err, cudaStream_t st);
+cudaError_t launch_init_lists(const int32_t *adj, int64_t n, int32_t r_in, int32_t offset,
+                              int32_t *out, int32_t R, cudaStream_t st);
+cudaError_t launch_fill(int32_t *p, int64_t count, int32_t value, cudaStream_t st);
+// Medoid: partial sums [nblk * dim] doubles, then argmin; result to *out (device).
+cudaError_t launch_medoid(const float *v, int64_t n, int32_t dim, int32_t metric, double *tmp,
+                          size_t tmp_bytes, int32_t *out, cudaStream_t st);
+size_t medoid_tmp_bytes(int64_t n, int32_t dim);
+
+}  // namespace rnsm

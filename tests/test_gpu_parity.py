@@ -1,0 +1,288 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Integer-valued (SIFT-like) inputs make every FP32 distance exact, so there
+the GPU must equal the oracle bit for bit.  On real-valued inputs distances
+must agree within a relative 1e-5, and result lists must agree except where
+the oracle logged a decision closer than that bound (a near tie)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from workloads import generators as gen
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def rn():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2602_17099_gb300 import build as b
+    b.build()
+    from paper_2602_17099_gb300 import rnsm
+    return rnsm
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    return t.cpu().numpy()
+
+
+_cache = {}
+
+
+def sift_graph(n, d=128, R=32, L=64, seed=3):
+    key = ("sift", n, d, R, L, seed)
+    if key not in _cache:
+        X = gen.sift_like(n, seed, d=d)
+        adj, ep = oracle.build_graph(X, R, L, 1.2)
+        _cache[key] = (X, adj, ep)
+    return _cache[key]
+
+
+def gauss_graph(n, d=32, R=16, L=32, seed=1):
+    key = ("gauss", n, d, R, L, seed)
+    if key not in _cache:
+        X = gen.gaussian(n, d, seed)
+        adj, ep = oracle.build_graph(X, R, L, 1.2)
+        _cache[key] = (X, adj, ep)
+    return _cache[key]
+
+
+# ------------------------------------------------------------------ search
+
+@pytest.mark.parametrize("ef,k,nseed", [(1, 1, 1), (17, 16, 1), (32, 10, 1), (64, 64, 1),
+                                        (100, 50, 3), (200, 200, 40), (256, 7, 64)])
+def test_search_exact_on_integer_data(rn, ef, k, nseed):
+    X, adj, ep = sift_graph(6000)
+    Q = gen.sift_like(517, 99, d=128)           # ragged: not a multiple of the warp count
+    rng = np.random.default_rng(ef)
+    seeds = rng.integers(-1, len(X), size=(len(Q), nseed)).astype(np.int32)
+    seeds[:, 0] = ep
+    want, wd, wndc, _, _ = oracle.beam_search(X, adj, Q, seeds, ef, k)
+    ids, dd, ndc = rn.search(dev(X), dev(adj), dev(Q), dev(seeds), ef, k, want_ndc=True)
+    np.testing.assert_array_equal(host(ids), want)
+    ok = want >= 0
+    np.testing.assert_array_equal(host(dd)[ok], wd[ok].astype(np.float32))
+    # the visited hash is exact until it overflows: NDC can only exceed the oracle's
+    assert (host(ndc) >= wndc).all()
+    assert (host(ndc) == wndc).mean() > 0.99
+
+
+@pytest.mark.parametrize("metric", [oracle.L2, oracle.IP])
+def test_search_float_data_within_tolerance(rn, metric):
+    if metric == oracle.L2:
+        X, adj, ep = gauss_graph(5000)
+        Q = gen.gaussian(1000, 32, 2)
+    else:
+        X = gen.deep_like(5000, 21, d=96)
+        adj, ep = oracle.build_graph(X, 16, 32, 1.2, metric=oracle.IP)
+        Q = gen.deep_like(1000, 22, d=96)
+    seeds = np.full((len(Q), 1), ep, np.int32)
+    want, wd, _, _, margin = oracle.beam_search(X, adj, Q, seeds, 48, 32, metric)
+    ids, dd, _ = rn.search(dev(X), dev(adj), dev(Q), dev(seeds), 48, 32, metric=metric)
+    ids, dd = host(ids), host(dd)
+    same = (ids == want).all(axis=1)
+    decided = margin > TOL
+    assert same[decided].all(), f"{(~same[decided]).sum()} decided queries differ"
+    # distances of identical ids agree within the relative bound
+    m = (ids == want) & (want >= 0)
+    rel = np.abs(dd[m] - wd[m]) / np.maximum(np.abs(wd[m]), 1e-30)
+    if metric == oracle.IP:   # 1 - <x,y>: the error is absolute in <x,y>
+        rel = np.abs(dd[m] - wd[m])
+    assert rel.max() <= TOL
+    assert same.mean() > 0.97
+
+
+def test_search_edge_cases(rn):
+    # one vertex; an empty graph (no edges); seeds all -1; duplicates of the entry
+    X = gen.sift_like(50, 7, d=32)
+    empty = np.full((50, 8), -1, np.int32)
+    Q = X[:5].copy()
+    seeds = np.array([[3, 3, -1], [-1, -1, -1], [0, 1, 2], [49, 48, 47], [10, -1, 10]], np.int32)
+    want, _, _, _, _ = oracle.beam_search(X, empty, Q, seeds, 4, 4)
+    ids, _, _ = rn.search(dev(X), dev(empty), dev(Q), dev(seeds), 4, 4)
+    np.testing.assert_array_equal(host(ids), want)
+    one = X[:1].copy()
+    ids, _, _ = rn.search(dev(one), dev(np.full((1, 4), -1, np.int32)), dev(Q), dev(
+        np.zeros((5, 1), np.int32)), 8, 3)
+    assert (host(ids)[:, 0] == 0).all() and (host(ids)[:, 1:] == -1).all()
+
+
+def test_expand_exact_on_integer_data(rn):
+    X, adj, _ = sift_graph(6000)
+    want, _, _, _ = oracle.expand(X, adj, 16)
+    got = rn.expand(dev(X), dev(adj), 16)
+    np.testing.assert_array_equal(host(got), want)
+
+
+def test_reverse_knn_bit_exact(rn):
+    X, adj, _ = sift_graph(6000)
+    nplus, _, _, _ = oracle.expand(X, adj, 16)
+    for k in (1, 5, 16):
+        wo, wi = oracle.reverse_knn(nplus, k)
+        go, gi = rn.reverse_knn(dev(nplus), k)
+        np.testing.assert_array_equal(host(go), wo)
+        np.testing.assert_array_equal(host(gi), wi)
+
+
+# ------------------------------------------------------------------- prune
+
+def _pools(n, w, seed, nown):
+    rng = np.random.default_rng(seed)
+    owners = rng.choice(n, nown, replace=False).astype(np.int32)
+    pool = rng.integers(-1, n, size=(nown, w)).astype(np.int32)
+    pool[:, 3] = owners          # the owner itself must be dropped
+    pool[:, 5] = pool[:, 4]      # duplicates must be dropped
+    return owners, pool
+
+
+@pytest.mark.parametrize("R,w,alpha", [(32, 64, 1.2), (16, 40, 1.0), (8, 200, 1.2),
+                                       (64, 128, 1.5), (32, 1000, 1.2), (5, 7, 2.0)])
+def test_prune_exact_on_integer_data(rn, R, w, alpha):
+    X = gen.sift_like(3000, 5, d=128)
+    owners, pool = _pools(3000, w, R + w, 301)
+    want, _ = oracle.prune(X, owners.astype(np.int64), pool, R, alpha)
+    got = rn.prune(dev(X), dev(owners), dev(pool), R, alpha)
+    np.testing.assert_array_equal(host(got), want)
+    want2, _ = oracle.prune(X, owners.astype(np.int64), pool, R, alpha, keep_all_if_fit=True)
+    got2 = rn.prune(dev(X), dev(owners), dev(pool), R, alpha, keep_all_if_fit=True)
+    np.testing.assert_array_equal(host(got2), want2)
+
+
+@pytest.mark.parametrize("d", [32, 96, 768])
+def test_prune_float_data_within_tolerance(rn, d):
+    X = gen.gaussian(2000, d, 9) if d == 32 else gen.deep_like(2000, 9, d=d)
+    owners, pool = _pools(2000, 96, d, 500)
+    want, margin = oracle.prune(X, owners.astype(np.int64), pool, 32, 1.2)
+    got = host(rn.prune(dev(X), dev(owners), dev(pool), 32, 1.2))
+    same = (got == want).all(axis=1)
+    assert same[margin > TOL].all()
+    assert same.mean() > 0.97
+
+
+def test_reverse_edges_exact_on_integer_data(rn):
+    X, adj, _ = sift_graph(6000)
+    n = len(X)
+    rng = np.random.default_rng(4)
+    ne = 40000
+    eu = rng.integers(0, n, ne).astype(np.int32)
+    ev = rng.integers(0, n, ne).astype(np.int32)
+    hub = eu[:3000].copy()
+    hub[:] = 17                   # one target with a large incoming pool
+    eu[:3000] = hub
+    keep = eu != ev
+    eu, ev = eu[keep], ev[keep]
+    pairs = np.unique(np.stack([eu, ev], 1), axis=0)
+    eu, ev = pairs[:, 0].copy(), pairs[:, 1].copy()
+    lists = adj.copy()
+    want = oracle.reverse_edges(X, lists, eu, ev, 1.2)
+    got = rn.reverse_edges(dev(X), dev(lists), dev(eu), dev(ev), 1.2)
+    np.testing.assert_array_equal(host(got), want)
+
+
+def test_medoid_matches_oracle(rn):
+    for X in (gen.sift_like(7777, 8, d=128), gen.gaussian(5000, 32, 3)):
+        assert rn.medoid(dev(X)) == oracle.medoid(X)
+
+
+def test_build_segment_exact_on_integer_data(rn):
+    X = gen.sift_like(4000, 12, d=32)
+    for bm in (64, 300):
+        want, wep = oracle.build_graph(X, 16, 32, 1.2, batch_max=bm)
+        got, gep = rn.build_segment(dev(X), 16, 32, 1.2, batch_max=bm)
+        assert gep == wep
+        np.testing.assert_array_equal(host(got), want)
+
+
+# ------------------------------------------------------------------- merge
+
+def _merge_both(rn, segs, graphs, entries, plan, R, L, **kw):
+    want, wst = oracle.rnsm_merge(segs, graphs, entries, [(a, b) for a, b, *_ in plan], R, L, 1.2,
+                                  **kw)
+    p = rn.params(R, L, 1.2, **{k: v for k, v in kw.items() if k in
+                                ("k_rev", "k_plus", "ef_slide", "c_cross", "metric")})
+    tsegs = [(dev(s), dev(g), e) for s, g, e in zip(segs, graphs, entries)]
+    got, gst = rn.merge(tsegs, p, plan)
+    return host(got), want, gst, wst
+
+
+def test_merge_pair_exact_on_integer_data(rn):
+    segs = [gen.sift_like(5000, 31, d=128), gen.sift_like(3100, 32, d=128)]
+    gs = [oracle.build_graph(s, 32, 64, 1.2) for s in segs]
+    got, want, gst, wst = _merge_both(rn, segs, [g for g, _ in gs], [e for _, e in gs],
+                                      [(1, 0)], 32, 64)
+    np.testing.assert_array_equal(got, want)
+    assert gst["pivots"] == wst["pivots"] and gst["followers"] == wst["followers"]
+    assert gst["reverse_edges"] == wst["reverse_edges"]
+    assert gst["ndc"] >= wst["ndc_expand"] + wst["ndc_search"]
+
+
+def test_merge_default_plan_and_parameters(rn):
+    segs = [gen.sift_like(1200, 41, d=32), gen.sift_like(1500, 42, d=32)]
+    gs = [oracle.build_graph(s, 16, 32, 1.2) for s in segs]
+    for kw in ({}, {"k_rev": 3, "k_plus": 8, "ef_slide": 20, "c_cross": 10}):
+        want, _ = oracle.rnsm_merge(segs, [g for g, _ in gs], [e for _, e in gs], [(0, 1)], 16, 32,
+                                    1.2, **kw)
+        tsegs = [(dev(s), dev(g), e) for s, (g, e) in zip(segs, gs)]
+        got, _ = rn.merge(tsegs, rn.params(16, 32, 1.2, **kw))   # plan=None: smaller -> larger
+        np.testing.assert_array_equal(host(got), want)
+
+
+def test_merge_multi_segment_plan_exact(rn):
+    sizes = [900, 1400, 600, 1100]
+    segs = [gen.sift_like(n, 50 + i, d=32) for i, n in enumerate(sizes)]
+    gs = [oracle.build_graph(s, 16, 32, 1.2) for s in segs]
+    cen = np.stack([s.astype(np.float64).mean(0) for s in segs]).astype(np.float32)
+    plan = oracle.mos_plan(sizes, cen)
+    assert plan == rn.mos_plan(sizes, cen)
+    got, want, _, _ = _merge_both(rn, segs, [g for g, _ in gs], [e for _, e in gs], plan, 16, 32)
+    np.testing.assert_array_equal(got, want)
+
+
+def test_merge_float_data_recall_within_tolerance(rn):
+    segs, Q = gen.tiny_case()
+    gs = [oracle.build_graph(s, 16, 32, 1.2) for s in segs]
+    got, want, _, _ = _merge_both(rn, segs, [g for g, _ in gs], [e for _, e in gs], [(1, 0)], 16,
+                                  32)
+    X = np.concatenate(segs)
+    _, gd = oracle.bruteforce_knn(X, Q, 10)
+    ep = np.full((len(Q), 1), gs[0][1], np.int32)
+    for ef in (16, 32, 64):
+        rw = oracle.recall_at_k(oracle.beam_search(X, want, Q, ep, ef, 10)[0], X, gd, Q)
+        rg = oracle.recall_at_k(oracle.beam_search(X, got, Q, ep, ef, 10)[0], X, gd, Q)
+        assert abs(rw - rg) <= 0.005, (ef, rw, rg)
+    assert (got == want).all(axis=1).mean() > 0.9
+
+
+def test_merge_cm_flag_runs_every_vertex_as_pivot(rn):
+    segs = [gen.sift_like(800, 61, d=32), gen.sift_like(900, 62, d=32)]
+    gs = [oracle.build_graph(s, 16, 32, 1.2) for s in segs]
+    tsegs = [(dev(s), dev(g), e) for s, (g, e) in zip(segs, gs)]
+    got, st = rn.merge(tsegs, rn.params(16, 32, 1.2, flags=rn.FLAG_CM))
+    assert st["pivots"] == 800 and st["followers"] == 0
+
+
+# ------------------------------------------------------------- validation
+
+def test_device_validation_errors(rn):
+    X = gen.sift_like(100, 1, d=32)
+    adj, ep = oracle.build_graph(X, 8, 16, 1.2)
+    bad = adj.copy()
+    bad[5, 2] = 100
+    with pytest.raises(rn.RnsmError) as e:
+        rn.merge([(dev(X), dev(bad), ep), (dev(X), dev(adj), ep)], rn.params(8, 16))
+    assert e.value.status == rn.EGRAPH
+    Xn = X.copy()
+    Xn[7, 3] = np.nan
+    with pytest.raises(rn.RnsmError) as e:
+        rn.merge([(dev(Xn), dev(adj), ep), (dev(X), dev(adj), ep)], rn.params(8, 16))
+    assert e.value.status == rn.EGRAPH
+    with pytest.raises(rn.RnsmError) as e:
+        rn.search(dev(X), dev(adj), dev(X[:3]), dev(np.array([[0], [100], [1]], np.int32)), 8, 4)
+    assert e.value.status == rn.EGRAPH
