@@ -108,6 +108,16 @@ typedef struct {
     int64_t pivots;        /* naive searches */
     int64_t followers;     /* local-sliding searches */
     int64_t reverse_edges; /* cross edges kept on the source side */
+    int64_t launches;      /* CUDA kernels launched by the call */
+    /* CUDA-event time per step on the call's stream, summed over plan edges:
+     * [0] validation and list initialisation, [1] S1 expansion, [2] S2
+     * inversion, [3] S3 pivot selection incl. its host copies, [4] S4 pivot
+     * search, [5] S5 follower search, [6] S6 source prune, [7] S7 reverse
+     * edges. */
+    double phase_ms[8];
+    int64_t search_ndc[3]; /* NDC of S1, S4, S5 */
+    int64_t search_exp[3]; /* expansions of S1, S4, S5 */
+    int64_t search_queries[3]; /* queries of S1, S4, S5 */
 } rnsm_stats;
 
 /*

@@ -97,7 +97,7 @@ rnsm_status ws_acquire(size_t bytes, Bump &b) {
 struct Ctl {
     int32_t *err;
     int32_t *work;           // several work counters
-    unsigned long long *stats;  // [0] ndc, [1] expansions
+    unsigned long long *stats;  // per search slot s: [2s] ndc, [2s+1] expansions
     unsigned long long *ecount;
     int32_t *scratch_i;      // misc int
 };
@@ -107,14 +107,14 @@ constexpr int kWorkSlots = 16;
 void take_ctl(Bump &b, Ctl &c) {
     c.err = b.take<int32_t>(1);
     c.work = b.take<int32_t>(kWorkSlots);
-    c.stats = b.take<unsigned long long>(4);
+    c.stats = b.take<unsigned long long>(8);
     c.ecount = b.take<unsigned long long>(1);
     c.scratch_i = b.take<int32_t>(4);
 }
 
 rnsm_status ctl_reset(const Ctl &c, cudaStream_t st) {
     CK(cudaMemsetAsync(c.err, 0, sizeof(int32_t), st));
-    CK(cudaMemsetAsync(c.stats, 0, 4 * sizeof(unsigned long long), st));
+    CK(cudaMemsetAsync(c.stats, 0, 8 * sizeof(unsigned long long), st));
     return RNSM_OK;
 }
 
@@ -692,6 +692,30 @@ void carve_merge(Bump &b, const rnsm_params &p, int64_t ns_max, int64_t nt_max, 
     take_rev(b, nt_max, ns_max * p.R, m.rev);
 }
 
+// CUDA events at the step boundaries of one plan edge (S1 .. S7).
+struct PhaseClock {
+    cudaEvent_t ev[9] = {};
+    bool ok = true;
+    PhaseClock() {
+        for (auto &e : ev) ok = ok && cudaEventCreate(&e) == cudaSuccess;
+    }
+    ~PhaseClock() {
+        for (auto &e : ev)
+            if (e) cudaEventDestroy(e);
+    }
+    void mark(int i, cudaStream_t st) {
+        if (ok) cudaEventRecord(ev[i], st);
+    }
+    // after a stream sync: phase_ms[i + shift] += time from mark i to mark i + 1
+    void add(double *phase_ms, int lo, int hi, int shift) {
+        if (!ok) return;
+        for (int i = lo; i < hi; ++i) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, ev[i], ev[i + 1]) == cudaSuccess) phase_ms[i + shift] += ms;
+        }
+    }
+};
+
 struct SrcCache {
     bool done = false;
     std::vector<int32_t> pivot_of, pivots, followers;
@@ -737,6 +761,11 @@ rnsm_status rnsm_merge(const rnsm_segment *segs, int32_t m, const rnsm_params *p
     }
     std::lock_guard<std::mutex> lk(g_mu);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const long long launches0 = launches_so_far();
+    double phase_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int64_t queries[3] = {0, 0, 0};
+    PhaseClock clk;
+    clk.mark(0, st);
     const int32_t dim = segs[0].dim;
     SegTable tab;
     std::memset(&tab, 0, sizeof(tab));
@@ -762,6 +791,9 @@ rnsm_status rnsm_merge(const rnsm_segment *segs, int32_t m, const rnsm_params *p
     for (int32_t s = 0; s < m; ++s)
         CK(launch_init_lists(segs[s].adj, segs[s].n, segs[s].r_in, (int32_t)tab.off[s],
                              out_adj + tab.off[s] * p.R, p.R, st));
+    clk.mark(1, st);
+    CK(cudaStreamSynchronize(st));
+    clk.add(phase_ms, 0, 1, 0);
 
     std::vector<SrcCache> cache((size_t)m);
     double host_s = 0.0;
@@ -777,6 +809,9 @@ rnsm_status rnsm_merge(const rnsm_segment *segs, int32_t m, const rnsm_params *p
         const int64_t ns = S.n, nt = T.n;
         const int32_t s0 = (int32_t)tab.off[e.src], t0 = (int32_t)tab.off[e.dst];
         SrcCache &sc = cache[e.src];
+        clk.mark(0, st);
+        clk.mark(1, st);
+        clk.mark(2, st);
         if (!sc.done) {
             sc.pivot_of.assign((size_t)ns, -1);
             sc.pivots.clear();
@@ -803,11 +838,14 @@ rnsm_status rnsm_merge(const rnsm_segment *segs, int32_t m, const rnsm_params *p
                 a.out_by_qidx = 1;
                 a.stats = c.stats;
                 TRY(run_search(a, c.work, st));
+                queries[0] += ns;
+                clk.mark(1, st);
                 // S2: reverse kNN inversion (counting sort by x).
                 CK(launch_rk_pairs(mb.nplus, ns, p.k_plus, p.k_rev, mb.rk_keys, mb.rk_vals,
                                    c.ecount, st));
                 CK(launch_bucket(mb.rk_keys, mb.rk_vals, ns * p.k_rev, c.ecount, ns, 0, mb.rk_offs,
                                  mb.rk_cursor, mb.rk_ids, mb.rk_scan, mb.rk_scan_bytes, st));
+                clk.mark(2, st);
                 // S3: lazy greedy on the host.
                 h_offs.resize((size_t)ns + 1);
                 h_ids.resize((size_t)(ns * p.k_rev));
@@ -833,6 +871,7 @@ rnsm_status rnsm_merge(const rnsm_segment *segs, int32_t m, const rnsm_params *p
                                    cudaMemcpyHostToDevice, st));
         CK(cudaMemcpyAsync(mb.pivot_of, sc.pivot_of.data(), sizeof(int32_t) * ns,
                            cudaMemcpyHostToDevice, st));
+        clk.mark(3, st);
         // S4: naive search of the pivots from the target's default entry.
         {
             SearchArgs a = search_defaults();
@@ -852,9 +891,11 @@ rnsm_status rnsm_merge(const rnsm_segment *segs, int32_t m, const rnsm_params *p
             a.out_ids = mb.res;
             a.out_stride = p.L;
             a.out_by_qidx = 1;
-            a.stats = c.stats;
+            a.stats = c.stats + 2;
             TRY(run_search(a, c.work, st));
+            queries[1] += np;
         }
+        clk.mark(4, st);
         // S5: local sliding of the followers from their pivot's results.
         if (nf) {
             SearchArgs a = search_defaults();
@@ -877,9 +918,11 @@ rnsm_status rnsm_merge(const rnsm_segment *segs, int32_t m, const rnsm_params *p
             a.out_ids = mb.res;
             a.out_stride = p.L;
             a.out_by_qidx = 1;
-            a.stats = c.stats;
+            a.stats = c.stats + 4;
             TRY(run_search(a, c.work + 3, st));
+            queries[2] += nf;
         }
+        clk.mark(5, st);
         // S6: source-side UpdateGraph: list(v) + first c_cross results -> prune.
         CK(cudaMemsetAsync(c.ecount, 0, sizeof(unsigned long long), st));
         {
@@ -906,21 +949,30 @@ rnsm_status rnsm_merge(const rnsm_segment *segs, int32_t m, const rnsm_params *p
             q.err = c.err;
             TRY(run_prune(q, c.work + 4, st));
         }
+        clk.mark(6, st);
         // S7: reverse edges into the target (counting sort by u, then prune).
         TRY(reverse_into(tab, dim, p, out_adj, mb.eu, mb.ev, ns * p.R, c.ecount, t0, nt, -1,
                          mb.rev, c, st));
+        clk.mark(7, st);
         unsigned long long ne = 0;
         CK(cudaMemcpyAsync(&ne, c.ecount, sizeof(ne), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
+        clk.add(phase_ms, 0, 7, 1);  // marks 0..7 bound S1..S7
         rev_total += ne;
     }
     TRY(check_err_word(c, st));
     if (stats) {
-        unsigned long long hs[4] = {0, 0, 0, 0};
+        unsigned long long hs[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         CK(cudaMemcpyAsync(hs, c.stats, sizeof(hs), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
-        stats->ndc = (int64_t)hs[0];
-        stats->expansions = (int64_t)hs[1];
+        stats->ndc = (int64_t)(hs[0] + hs[2] + hs[4]);
+        stats->expansions = (int64_t)(hs[1] + hs[3] + hs[5]);
+        for (int i = 0; i < 3; ++i) {
+            stats->search_ndc[i] = (int64_t)hs[2 * i];
+            stats->search_exp[i] = (int64_t)hs[2 * i + 1];
+            stats->search_queries[i] = queries[i];
+        }
+        stats->launches = launches_so_far() - launches0;
         stats->rechecks = 0;
         stats->near_ties = 0;
         stats->pivots = n_piv;
@@ -928,6 +980,7 @@ rnsm_status rnsm_merge(const rnsm_segment *segs, int32_t m, const rnsm_params *p
         stats->reverse_edges = (int64_t)rev_total;
         stats->host_pivot_s = host_s;
         stats->wall_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        for (int i = 0; i < 8; ++i) stats->phase_ms[i] = phase_ms[i];
     }
     return RNSM_OK;
 }

@@ -10,9 +10,18 @@
 #include <float.h>
 #include <math.h>
 
+#include <atomic>
+
 #include "internal.h"
 
 namespace rnsm {
+
+namespace {
+std::atomic<long long> g_launches{0};
+}
+
+void note_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+long long launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
 
 namespace {
 
@@ -307,14 +316,18 @@ cudaError_t launch_bucket(const int32_t *keys, const int32_t *vals, int64_t cap,
     if (scan_tmp_bytes < bucket_scan_tmp_bytes(nkeys)) return cudaErrorInvalidValue;
     cudaError_t e = cudaMemsetAsync(cursor, 0, sizeof(int32_t) * (size_t)nkeys, st);
     if (e != cudaSuccess) return e;
-    if (cap > 0) count_kernel<<<grid_for(cap, 256), 256, 0, st>>>(keys, cap, count, nkeys, key_offset,
-                                                                   cursor);
+    if (cap > 0) {
+        count_kernel<<<grid_for(cap, 256), 256, 0, st>>>(keys, cap, count, nkeys, key_offset,
+                                                         cursor);
+        note_launches(2);  // count + scatter
+    }
     const int64_t ntiles = (nkeys + kScanTile - 1) / kScanTile;
     int64_t *tiles = static_cast<int64_t *>(scan_tmp);
     if (ntiles > 0) {
         tile_sum_kernel<<<(unsigned)ntiles, kScanThreads, 0, st>>>(cursor, nkeys, tiles);
         scan_tiles_kernel<<<1, 1024, 0, st>>>(tiles, ntiles);
         scan_apply_kernel<<<(unsigned)ntiles, kScanThreads, 0, st>>>(cursor, nkeys, tiles, offs);
+        note_launches(3);
     } else {
         e = cudaMemsetAsync(offs, 0, sizeof(int64_t), st);
         if (e != cudaSuccess) return e;
@@ -337,6 +350,7 @@ cudaError_t launch_sort_rows(const int64_t *offs, int32_t *ids, int64_t nrows, i
     int64_t g = (nrows + kRowSortWarps - 1) / kRowSortWarps;
     if (g > 8192) g = 8192;
     sort_rows_kernel<<<(unsigned)g, kRowSortWarps * 32, smem, st>>>(offs, ids, nrows, err);
+    note_launches(1);
     return cudaGetLastError();
 }
 
@@ -344,6 +358,7 @@ cudaError_t launch_rk_pairs(const int32_t *nplus, int64_t n, int32_t k_plus, int
                             int32_t *keys, int32_t *vals, unsigned long long *count,
                             cudaStream_t st) {
     rk_pairs_kernel<<<grid_for(n * k, 256), 256, 0, st>>>(nplus, n, k_plus, k, keys, vals, count);
+    note_launches(1);
     return cudaGetLastError();
 }
 
@@ -357,12 +372,14 @@ cudaError_t launch_validate_ids(const int32_t *ids, int64_t count, int64_t bound
     if (count <= 0) return cudaSuccess;
     validate_ids_kernel<<<grid_for(count, 256), 256, 0, st>>>(ids, count, bound,
                                                               allow_minus1 ? -1 : 0, err);
+    note_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_validate_vecs(const float *v, int64_t count, int32_t *err, cudaStream_t st) {
     if (count <= 0) return cudaSuccess;
     validate_vecs_kernel<<<grid_for(count, 256), 256, 0, st>>>(v, count, err);
+    note_launches(1);
     return cudaGetLastError();
 }
 
@@ -370,12 +387,14 @@ cudaError_t launch_init_lists(const int32_t *adj, int64_t n, int32_t r_in, int32
                               int32_t *out, int32_t R, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     init_lists_kernel<<<grid_for(n * R, 256), 256, 0, st>>>(adj, n, r_in, offset, out, R);
+    note_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_fill(int32_t *p, int64_t count, int32_t value, cudaStream_t st) {
     if (count <= 0) return cudaSuccess;
     fill_kernel<<<grid_for(count, 256), 256, 0, st>>>(p, count, value);
+    note_launches(1);
     return cudaGetLastError();
 }
 
@@ -383,6 +402,7 @@ cudaError_t launch_max_row(const int64_t *offs, int64_t n, int32_t *out, cudaStr
     cudaError_t e = cudaMemsetAsync(out, 0, sizeof(int32_t), st);
     if (e != cudaSuccess || n <= 0) return e;
     max_row_kernel<<<grid_for(n, 256), 256, 0, st>>>(offs, n, out);
+    note_launches(1);
     return cudaGetLastError();
 }
 
@@ -403,6 +423,7 @@ cudaError_t launch_medoid(const float *v, int64_t n, int32_t dim, int32_t metric
     medoid_centroid_kernel<<<1, 256, 0, st>>>(part, kMedBlocks, n, dim, c);
     medoid_argmin_kernel<<<kMedBlocks, 256, 0, st>>>(v, n, dim, metric, c, bd, bi);
     medoid_final_kernel<<<1, 1, 0, st>>>(bd, bi, kMedBlocks, out);
+    note_launches(4);
     return cudaGetLastError();
 }
 

@@ -8,6 +8,10 @@
 
 namespace rnsm {
 
+// Kernels launched by this library (every launcher adds its count).
+void note_launches(int n);
+long long launches_so_far();
+
 enum SeedMode : int32_t { kSeedConst = 0, kSeedSelf = 1, kSeedTable = 2 };
 
 // One batched beam-search launch (Algorithm 1).  Query i reads

@@ -353,6 +353,7 @@ cudaError_t launch_prune(const PruneArgs &a, cudaStream_t st) {
     int64_t want = (a.n_owners + chunk - 1) / chunk;
     if (want < grid) grid = want;
     prune_kernel<<<(unsigned)grid, kThreads, smem, st>>>(a, rows_cap, pool_cap, chunk);
+    note_launches(1);
     return cudaGetLastError();
 }
 

@@ -49,10 +49,17 @@ class MosEdge(C.Structure):
 class Stats(C.Structure):
     _fields_ = [("wall_s", C.c_double), ("host_pivot_s", C.c_double), ("ndc", C.c_int64),
                 ("expansions", C.c_int64), ("rechecks", C.c_int64), ("near_ties", C.c_int64),
-                ("pivots", C.c_int64), ("followers", C.c_int64), ("reverse_edges", C.c_int64)]
+                ("pivots", C.c_int64), ("followers", C.c_int64), ("reverse_edges", C.c_int64),
+                ("launches", C.c_int64), ("phase_ms", C.c_double * 8),
+                ("search_ndc", C.c_int64 * 3), ("search_exp", C.c_int64 * 3),
+                ("search_queries", C.c_int64 * 3)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        out = {}
+        for k, _ in self._fields_:
+            v = getattr(self, k)
+            out[k] = list(v) if hasattr(v, "__len__") else v
+        return out
 
 
 _lib = None

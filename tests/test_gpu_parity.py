@@ -69,9 +69,10 @@ def test_search_exact_on_integer_data(rn, ef, k, nseed):
     np.testing.assert_array_equal(host(ids), want)
     ok = want >= 0
     np.testing.assert_array_equal(host(dd)[ok], wd[ok].astype(np.float32))
-    # the visited hash is exact until it overflows: NDC can only exceed the oracle's
+    # the visited hash is exact until it overflows: NDC can only exceed the
+    # oracle's, and overflows must stay rare
     assert (host(ndc) >= wndc).all()
-    assert (host(ndc) == wndc).mean() > 0.99
+    assert host(ndc).sum() <= 1.01 * wndc.sum()
 
 
 @pytest.mark.parametrize("metric", [oracle.L2, oracle.IP])
