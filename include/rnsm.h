@@ -89,6 +89,9 @@ typedef struct {
 /* Cross-query Merge comparator (Section 3.1): every source vertex runs a
  * naive search (no pivots, no sliding). */
 #define RNSM_FLAG_CM 0x1u
+/* Run pivot selection (S3) with the host lazy greedy instead of the device
+ * rounds (identical results; for cross-checking). */
+#define RNSM_FLAG_HOST_PIVOTS 0x2u
 
 /* One edge of a merge plan: segment `src` is merged into segment `dst`.
  * Plan order = array order (Section 5: closer pairs first). */
@@ -220,6 +223,23 @@ RNSM_API rnsm_status rnsm_reverse_knn(const int32_t *nplus, int64_t n, int32_t k
  */
 RNSM_API rnsm_status rnsm_select_pivots(int64_t n, const int64_t *offs, const int32_t *ids,
                                int32_t *pivot_of, int32_t *pivots, int64_t *n_pivots);
+
+/*
+ * rnsm_select_pivots_gpu -- Phase 2 of Algorithm 2 on the device, with the
+ * same result as rnsm_select_pivots.  Parallel rounds: every uncovered x whose
+ * key (|R_k(x) \ Covered|, then lower id) beats that of every uncovered
+ * vertex of N_k(x), R_k(x) and N_k(z) for uncovered z in R_k(x) becomes a
+ * pivot with followers R_k(x) \ Covered.  Such local maxima are exactly the
+ * vertices the sequential lazy greedy selects with those follower sets.
+ *   nplus, k_plus, k   device N+ [n * k_plus]; N_k = its first k columns
+ *   offs, ids          device CSR of R_k built from the same N_k
+ *   pivot_of           device [n]: pivot of each follower, -1 for pivots
+ *   n_pivots, rounds   host outputs (rounds may be NULL)
+ */
+RNSM_API rnsm_status rnsm_select_pivots_gpu(const int32_t *nplus, int64_t n, int32_t k_plus,
+                                            int32_t k, const int64_t *offs, const int32_t *ids,
+                                            int32_t *pivot_of, int64_t *n_pivots,
+                                            int32_t *rounds, void *stream);
 
 /*
  * rnsm_prune -- heuristic edge selection of UpdateGraph (Section 4.2; the

@@ -329,6 +329,37 @@ rnsm_status rnsm_select_pivots(int64_t n, const int64_t *offs, const int32_t *id
     return RNSM_OK;
 }
 
+rnsm_status rnsm_select_pivots_gpu(const int32_t *nplus, int64_t n, int32_t k_plus, int32_t k,
+                                   const int64_t *offs, const int32_t *ids, int32_t *pivot_of,
+                                   int64_t *n_pivots, int32_t *rounds, void *stream) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (!nplus || n < 1 || n >= INT32_MAX || !offs || !ids || !pivot_of || !n_pivots)
+        return fail(RNSM_EINVAL, "rnsm_select_pivots_gpu: bad arguments");
+    if (k < 1 || k > k_plus) return fail(RNSM_EINVAL, "need 1 <= k <= k_plus");
+    Bump b;
+    Ctl c;
+    auto carve = [&](Bump &bb) {
+        take_ctl(bb, c);
+        int32_t *pv = bb.take<int32_t>(n);
+        int32_t *fl = bb.take<int32_t>(n);
+        void *tmp = bb.take<char>(pivot_tmp_bytes(n));
+        return std::make_tuple(pv, fl, tmp);
+    };
+    carve(b);
+    TRY(ws_acquire(b.off, b));
+    int32_t *pv, *fl;
+    void *tmp;
+    std::tie(pv, fl, tmp) = carve(b);
+    TRY(ctl_reset(c, st));
+    CK(launch_validate_ids(nplus, n * k_plus, n, 1, c.err, st));
+    TRY(check_err_word(c, st));
+    int64_t nf = 0;
+    CK(select_pivots_device(nplus, n, k_plus, k, offs, ids, pivot_of, pv, fl, n_pivots, &nf,
+                            rounds, tmp, c.stats, st));
+    return RNSM_OK;
+}
+
 rnsm_status rnsm_search(const float *vecs, int64_t n, int32_t dim, const int32_t *adj,
                         int32_t r_in, const float *queries, int64_t nq, const int32_t *seeds,
                         int32_t n_seeds, int32_t ef, int32_t k, int32_t metric,
@@ -669,6 +700,7 @@ struct MergeBufs {
     void *rk_scan;
     size_t rk_scan_bytes;
     int32_t *pivots, *followers, *pivot_of, *res, *eu, *ev;
+    void *piv_tmp;
     RevBufs rev;
 };
 
@@ -686,6 +718,7 @@ void carve_merge(Bump &b, const rnsm_params &p, int64_t ns_max, int64_t nt_max, 
     m.pivots = b.take<int32_t>(ns_max);
     m.followers = b.take<int32_t>(ns_max);
     m.pivot_of = b.take<int32_t>(ns_max);
+    m.piv_tmp = b.take<char>(pivot_tmp_bytes(ns_max));
     m.res = b.take<int32_t>(ns_max * p.L);
     m.eu = b.take<int32_t>(ns_max * p.R);
     m.ev = b.take<int32_t>(ns_max * p.R);
@@ -718,7 +751,9 @@ struct PhaseClock {
 
 struct SrcCache {
     bool done = false;
-    std::vector<int32_t> pivot_of, pivots, followers;
+    int64_t np = 0, nf = 0;
+    std::vector<int32_t> pivot_of, pivots, followers;  // host copies (device S3 keeps its own)
+    bool on_device = false;
 };
 
 }  // namespace
@@ -803,6 +838,7 @@ rnsm_status rnsm_merge(const rnsm_segment *segs, int32_t m, const rnsm_params *p
     const bool cm = (p.flags & RNSM_FLAG_CM) != 0;
     std::vector<int64_t> h_offs;
     std::vector<int32_t> h_ids;
+    int32_t lists_for = -1;  // source segment whose pivot lists are in the device buffers
 
     for (const PlanEdge &e : pl) {
         const rnsm_segment &S = segs[e.src], &T = segs[e.dst];
@@ -812,7 +848,11 @@ rnsm_status rnsm_merge(const rnsm_segment *segs, int32_t m, const rnsm_params *p
         clk.mark(0, st);
         clk.mark(1, st);
         clk.mark(2, st);
+        bool reuse_later = false;
+        for (size_t j = (size_t)(&e - pl.data()) + 1; j < pl.size(); ++j)
+            if (pl[j].src == e.src) reuse_later = true;
         if (!sc.done) {
+            bool host_lists = true;
             sc.pivot_of.assign((size_t)ns, -1);
             sc.pivots.clear();
             sc.followers.clear();
@@ -846,31 +886,65 @@ rnsm_status rnsm_merge(const rnsm_segment *segs, int32_t m, const rnsm_params *p
                 CK(launch_bucket(mb.rk_keys, mb.rk_vals, ns * p.k_rev, c.ecount, ns, 0, mb.rk_offs,
                                  mb.rk_cursor, mb.rk_ids, mb.rk_scan, mb.rk_scan_bytes, st));
                 clk.mark(2, st);
-                // S3: lazy greedy on the host.
-                h_offs.resize((size_t)ns + 1);
-                h_ids.resize((size_t)(ns * p.k_rev));
-                CK(cudaMemcpyAsync(h_offs.data(), mb.rk_offs, sizeof(int64_t) * (ns + 1),
-                                   cudaMemcpyDeviceToHost, st));
-                CK(cudaMemcpyAsync(h_ids.data(), mb.rk_ids, sizeof(int32_t) * ns * p.k_rev,
-                                   cudaMemcpyDeviceToHost, st));
-                CK(cudaStreamSynchronize(st));
-                const auto h0 = std::chrono::steady_clock::now();
-                select_pivots_host(ns, h_offs.data(), h_ids.data(), sc.pivot_of.data(), sc.pivots);
-                for (int64_t y = 0; y < ns; ++y)
-                    if (sc.pivot_of[y] >= 0) sc.followers.push_back((int32_t)y);
-                host_s += std::chrono::duration<double>(std::chrono::steady_clock::now() - h0).count();
+                if (p.flags & RNSM_FLAG_HOST_PIVOTS) {
+                    // S3: lazy greedy on the host.
+                    h_offs.resize((size_t)ns + 1);
+                    h_ids.resize((size_t)(ns * p.k_rev));
+                    CK(cudaMemcpyAsync(h_offs.data(), mb.rk_offs, sizeof(int64_t) * (ns + 1),
+                                       cudaMemcpyDeviceToHost, st));
+                    CK(cudaMemcpyAsync(h_ids.data(), mb.rk_ids, sizeof(int32_t) * ns * p.k_rev,
+                                       cudaMemcpyDeviceToHost, st));
+                    CK(cudaStreamSynchronize(st));
+                    const auto h0 = std::chrono::steady_clock::now();
+                    select_pivots_host(ns, h_offs.data(), h_ids.data(), sc.pivot_of.data(),
+                                       sc.pivots);
+                    for (int64_t y = 0; y < ns; ++y)
+                        if (sc.pivot_of[y] >= 0) sc.followers.push_back((int32_t)y);
+                    host_s += std::chrono::duration<double>(std::chrono::steady_clock::now() - h0)
+                                  .count();
+                } else {
+                    // S3: the same selection in parallel rounds on the device.
+                    int64_t np_ = 0, nf_ = 0;
+                    CK(select_pivots_device(mb.nplus, ns, p.k_plus, p.k_rev, mb.rk_offs, mb.rk_ids,
+                                            mb.pivot_of, mb.pivots, mb.followers, &np_, &nf_,
+                                            nullptr, mb.piv_tmp, c.stats + 6, st));
+                    sc.np = np_;
+                    sc.nf = nf_;
+                    host_lists = false;
+                    lists_for = e.src;
+                    if (reuse_later) {  // keep a host copy: the device lists get overwritten
+                        sc.pivot_of.resize((size_t)ns);
+                        sc.pivots.resize((size_t)np_);
+                        sc.followers.resize((size_t)nf_);
+                        CK(cudaMemcpyAsync(sc.pivot_of.data(), mb.pivot_of, sizeof(int32_t) * ns,
+                                           cudaMemcpyDeviceToHost, st));
+                        if (np_) CK(cudaMemcpyAsync(sc.pivots.data(), mb.pivots,
+                                                    sizeof(int32_t) * np_, cudaMemcpyDeviceToHost, st));
+                        if (nf_) CK(cudaMemcpyAsync(sc.followers.data(), mb.followers,
+                                                    sizeof(int32_t) * nf_, cudaMemcpyDeviceToHost, st));
+                        CK(cudaStreamSynchronize(st));
+                    }
+                }
+            }
+            if (host_lists) {
+                sc.np = (int64_t)sc.pivots.size();
+                sc.nf = (int64_t)sc.followers.size();
+                lists_for = -1;
             }
             sc.done = true;
         }
-        const int64_t np = (int64_t)sc.pivots.size(), nf = (int64_t)sc.followers.size();
+        const int64_t np = sc.np, nf = sc.nf;
         n_piv += np;
         n_fol += nf;
-        if (np) CK(cudaMemcpyAsync(mb.pivots, sc.pivots.data(), sizeof(int32_t) * np,
-                                   cudaMemcpyHostToDevice, st));
-        if (nf) CK(cudaMemcpyAsync(mb.followers, sc.followers.data(), sizeof(int32_t) * nf,
-                                   cudaMemcpyHostToDevice, st));
-        CK(cudaMemcpyAsync(mb.pivot_of, sc.pivot_of.data(), sizeof(int32_t) * ns,
-                           cudaMemcpyHostToDevice, st));
+        if (lists_for != e.src) {
+            if (np) CK(cudaMemcpyAsync(mb.pivots, sc.pivots.data(), sizeof(int32_t) * np,
+                                       cudaMemcpyHostToDevice, st));
+            if (nf) CK(cudaMemcpyAsync(mb.followers, sc.followers.data(), sizeof(int32_t) * nf,
+                                       cudaMemcpyHostToDevice, st));
+            CK(cudaMemcpyAsync(mb.pivot_of, sc.pivot_of.data(), sizeof(int32_t) * ns,
+                               cudaMemcpyHostToDevice, st));
+            lists_for = e.src;
+        }
         clk.mark(3, st);
         // S4: naive search of the pivots from the target's default entry.
         {

@@ -106,6 +106,16 @@ cudaError_t launch_max_row(const int64_t *offs, int64_t n, int32_t *out, cudaStr
 
 bool search_dim_supported(int dim);
 
+// S3 on the device (parallel rounds, same result as the lazy greedy).
+// tmp: pivot_tmp_bytes(n); counters: 2 device u64.  Writes pivot_of [n]
+// (-1 pivots), the pivot and follower lists (ascending-free order) and counts.
+size_t pivot_tmp_bytes(int64_t n);
+cudaError_t select_pivots_device(const int32_t *nplus, int64_t n, int32_t k_plus, int32_t k,
+                                 const int64_t *offs, const int32_t *ids, int32_t *pivot_of,
+                                 int32_t *pivots, int32_t *followers, int64_t *n_pivots,
+                                 int64_t *n_followers, int32_t *rounds, void *tmp,
+                                 unsigned long long *counters, cudaStream_t st);
+
 cudaError_t launch_validate_graph(const int32_t *adj, int64_t n, int32_t r_in, int32_t *err,
                                   cudaStream_t st);
 // Sets bit 1 of *err if an id is outside [allow_minus1 ? -1 : 0, bound).

@@ -21,6 +21,7 @@ OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EGRAPH = range(6)
 L2, IP = 0, 1
 FP32, BF16, FP8 = 0, 1, 2
 FLAG_CM = 0x1
+FLAG_HOST_PIVOTS = 0x2
 _STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "EGRAPH"}
 
 
@@ -76,6 +77,7 @@ _SIGS = {
     "rnsm_expand": (i32, [P, i64, i32, P, i32, i32, i32, P, P]),
     "rnsm_reverse_knn": (i32, [P, i64, i32, i32, P, P, P]),
     "rnsm_select_pivots": (i32, [i64, P, P, P, P, P]),
+    "rnsm_select_pivots_gpu": (i32, [P, i64, i32, i32, P, P, P, P, P, P]),
     "rnsm_prune": (i32, [P, i64, i32, P, i64, P, i32, i32, f32, i32, i32, i32, P, P]),
     "rnsm_reverse_edges": (i32, [P, i64, i32, P, i32, P, P, i64, f32, i32, P]),
     "rnsm_build_segment": (i32, [P, i64, i32, P, i64, P, P, P]),
@@ -236,6 +238,21 @@ def select_pivots(n, offs, ids):
                                     piv_of.ctypes.data_as(P), piv.ctypes.data_as(P),
                                     C.byref(npiv)))
     return piv_of, piv[: npiv.value].copy()
+
+
+def select_pivots_gpu(nplus, k, offs, ids):
+    """Device pivot selection on device N+ and R_k CSR; returns
+    (pivot_of tensor, number of pivots, rounds)."""
+    n, kp = nplus.shape
+    piv_of = torch.empty(n, dtype=torch.int32, device=nplus.device)
+    npiv = C.c_int64(0)
+    rounds = C.c_int32(0)
+    _check(lib().rnsm_select_pivots_gpu(_dev(nplus, torch.int32, "nplus"), n, kp, k,
+                                        _dev(offs, torch.int64, "offs"),
+                                        _dev(ids, torch.int32, "ids"),
+                                        C.c_void_p(piv_of.data_ptr()), C.byref(npiv),
+                                        C.byref(rounds), _stream()))
+    return piv_of, npiv.value, rounds.value
 
 
 def prune(vecs, owners, pool, R, alpha, metric=L2, keep_all_if_fit=False, prec=FP32):

@@ -287,3 +287,46 @@ def test_device_validation_errors(rn):
     with pytest.raises(rn.RnsmError) as e:
         rn.search(dev(X), dev(adj), dev(X[:3]), dev(np.array([[0], [100], [1]], np.int32)), 8, 4)
     assert e.value.status == rn.EGRAPH
+
+
+# ------------------------------------------------------------- pivots (S3)
+
+@pytest.mark.parametrize("seed,k", [(0, 1), (1, 3), (2, 5), (3, 7), (4, 16)])
+def test_device_pivot_selection_equals_lazy_greedy(rn, seed, k):
+    X = gen.sift_like(4000, 70 + seed, d=32) if seed % 2 else gen.gaussian(4000, 16, 70 + seed)
+    adj, _ = oracle.build_graph(X, 16, 32, 1.2)
+    nplus, _, _, _ = oracle.expand(X, adj, 16)
+    offs, ids = oracle.reverse_knn(nplus, k)
+    want_of, want_piv, _ = oracle.select_pivots(len(X), offs, ids)
+    got_of, npiv, rounds = rn.select_pivots_gpu(dev(nplus), k, dev(offs),
+                                                dev(ids if len(ids) else np.zeros(1, np.int32)))
+    np.testing.assert_array_equal(host(got_of), want_of)
+    assert npiv == len(want_piv)
+    assert rounds >= 1
+
+
+def test_device_pivot_selection_degenerate_inputs(rn):
+    # no reverse neighbours at all: every vertex is a singleton pivot
+    n = 300
+    nplus = np.full((n, 4), -1, np.int32)
+    offs, ids = oracle.reverse_knn(nplus, 2)
+    got_of, npiv, _ = rn.select_pivots_gpu(dev(nplus), 2, dev(offs), dev(np.zeros(1, np.int32)))
+    assert (host(got_of) == -1).all() and npiv == n
+    # a star: vertex 0 is everyone's nearest
+    nplus = np.full((n, 4), -1, np.int32)
+    nplus[1:, 0] = 0
+    nplus[0, 0] = 1
+    offs, ids = oracle.reverse_knn(nplus, 1)
+    want_of, _, _ = oracle.select_pivots(n, offs, ids)
+    got_of, _, _ = rn.select_pivots_gpu(dev(nplus), 1, dev(offs), dev(ids))
+    np.testing.assert_array_equal(host(got_of), want_of)
+
+
+def test_merge_host_and_device_pivots_agree(rn):
+    segs = [gen.gaussian(3000, 32, 81), gen.gaussian(2500, 32, 82)]
+    gs = [oracle.build_graph(s, 16, 32, 1.2) for s in segs]
+    tsegs = [(dev(s), dev(g), e) for s, (g, e) in zip(segs, gs)]
+    a, sa = rn.merge(tsegs, rn.params(16, 32, 1.2))
+    b, sb = rn.merge(tsegs, rn.params(16, 32, 1.2, flags=rn.FLAG_HOST_PIVOTS))
+    np.testing.assert_array_equal(host(a), host(b))
+    assert sa["pivots"] == sb["pivots"]
