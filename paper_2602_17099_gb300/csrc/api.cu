@@ -96,6 +96,8 @@ rnsm_status ws_acquire(size_t bytes, Bump &b) {
 // Small per-call device state at the head of the workspace.
 struct Ctl {
     int32_t *err;
+    int32_t *ovf;            // owners passed from the small-pool prune to the general one
+    unsigned long long *ovf_count;
     int32_t *work;           // several work counters
     unsigned long long *stats;  // per search slot s: [2s] ndc, [2s+1] expansions
     unsigned long long *ecount;
@@ -104,8 +106,10 @@ struct Ctl {
 
 constexpr int kWorkSlots = 16;
 
-void take_ctl(Bump &b, Ctl &c) {
+void take_ctl(Bump &b, Ctl &c, int64_t max_owners = 0) {
     c.err = b.take<int32_t>(1);
+    c.ovf = max_owners > 0 ? b.take<int32_t>(max_owners) : nullptr;
+    c.ovf_count = b.take<unsigned long long>(1);
     c.work = b.take<int32_t>(kWorkSlots);
     c.stats = b.take<unsigned long long>(8);
     c.ecount = b.take<unsigned long long>(1);
@@ -210,9 +214,12 @@ PruneArgs prune_defaults() {
     return a;
 }
 
-rnsm_status run_prune(PruneArgs a, int32_t *work, cudaStream_t st) {
-    CK(cudaMemsetAsync(work, 0, sizeof(int32_t), st));
+rnsm_status run_prune(PruneArgs a, int32_t *work, const Ctl &c, cudaStream_t st) {
+    CK(cudaMemsetAsync(work, 0, 2 * sizeof(int32_t), st));
     a.work = work;
+    a.work2 = work + 1;
+    a.ovf_list = c.ovf;
+    a.ovf_count = c.ovf_count;
     CK(launch_prune(a, st));
     return RNSM_OK;
 }
@@ -265,7 +272,7 @@ rnsm_status reverse_into(const SegTable &tab, int32_t dim, const rnsm_params &p,
     a.csr_max = csr_max;
     a.out = lists;
     a.err = c.err;
-    return run_prune(a, c.work + 1, st);
+    return run_prune(a, c.work + 6, c, st);
 }
 
 }  // namespace
@@ -493,9 +500,9 @@ rnsm_status rnsm_prune(const float *vecs, int64_t n, int32_t dim, const int32_t 
     if (nv == 0) return RNSM_OK;
     Bump b;
     Ctl c;
-    take_ctl(b, c);
+    take_ctl(b, c, nv);
     TRY(ws_acquire(b.off, b));
-    take_ctl(b, c);
+    take_ctl(b, c, nv);
     TRY(ctl_reset(c, st));
     TRY(validate_on_device(vecs, n, dim, nullptr, 0, c, st));
     CK(launch_validate_ids(owners, nv, n, 0, c.err, st));
@@ -522,7 +529,7 @@ rnsm_status rnsm_prune(const float *vecs, int64_t n, int32_t dim, const int32_t 
     a.out = out;
     a.out_by_index = 1;
     a.err = c.err;
-    TRY(run_prune(a, c.work, st));
+    TRY(run_prune(a, c.work + 8, c, st));
     TRY(check_err_word(c, st));
     return RNSM_OK;
 }
@@ -541,10 +548,10 @@ rnsm_status rnsm_reverse_edges(const float *vecs, int64_t n, int32_t dim, int32_
     Bump b;
     Ctl c;
     RevBufs r;
-    take_ctl(b, c);
+    take_ctl(b, c, n);
     take_rev(b, n, ne, r);
     TRY(ws_acquire(b.off, b));
-    take_ctl(b, c);
+    take_ctl(b, c, n);
     take_rev(b, n, ne, r);
     TRY(ctl_reset(c, st));
     TRY(validate_on_device(vecs, n, dim, lists, R, c, st));
@@ -607,7 +614,7 @@ rnsm_status rnsm_build_segment(const float *vecs, int64_t n, int32_t dim, const 
     RevBufs r;
     const int64_t B = batch_max;
     auto carve = [&](Bump &bb) {
-        take_ctl(bb, c);
+        take_ctl(bb, c, n);
         int32_t *order = bb.take<int32_t>(n);
         int32_t *cand = bb.take<int32_t>(B * p.L);
         int32_t *eu = bb.take<int32_t>(B * p.R);
@@ -677,7 +684,7 @@ rnsm_status rnsm_build_segment(const float *vecs, int64_t n, int32_t dim, const 
         q.ev = ev;
         q.ecount = c.ecount;
         q.err = c.err;
-        TRY(run_prune(q, c.work + 2, st));
+        TRY(run_prune(q, c.work + 8, c, st));
         TRY(reverse_into(tab, dim, p, out_adj, eu, ev, bsz * p.R, c.ecount, 0, n, (int32_t)bsz, r,
                          c, st));
         inserted += bsz;
@@ -706,7 +713,7 @@ struct MergeBufs {
 
 void carve_merge(Bump &b, const rnsm_params &p, int64_t ns_max, int64_t nt_max, Ctl &c,
                  MergeBufs &m) {
-    take_ctl(b, c);
+    take_ctl(b, c, ns_max > nt_max ? ns_max : nt_max);
     m.nplus = b.take<int32_t>(ns_max * p.k_plus);
     m.rk_keys = b.take<int32_t>(ns_max * p.k_rev);
     m.rk_vals = b.take<int32_t>(ns_max * p.k_rev);
@@ -1021,7 +1028,7 @@ rnsm_status rnsm_merge(const rnsm_segment *segs, int32_t m, const rnsm_params *p
             q.ev = mb.ev;
             q.ecount = c.ecount;
             q.err = c.err;
-            TRY(run_prune(q, c.work + 4, st));
+            TRY(run_prune(q, c.work + 8, c, st));
         }
         clk.mark(6, st);
         // S7: reverse edges into the target (counting sort by u, then prune).

@@ -78,6 +78,9 @@ struct PruneArgs {
     int32_t *ev;
     unsigned long long *ecount;
     int32_t *work;
+    int32_t *work2;           // second zeroed counter (overflow pass)
+    int32_t *ovf_list;        // [n_owners]: owners whose pool exceeds the small-pool kernel
+    unsigned long long *ovf_count;
     int32_t *err;             // bit 4: pool larger than the capacity
 };
 

@@ -1,16 +1,21 @@
 // K2: occlusion prune of UpdateGraph (Section 4.2; the RNG-variant edge
 // selection of Section 2.2), one CTA per owner vertex, persistent.
 //
-// For owner v with pool W: gather and deduplicate W (drop v and -1),
-// compute d(v, c) for every candidate, sort by (d, id), then walk the order
-// in tile passes.  A pass stages the rows of the candidates kept so far plus
-// the next chunk of up to 64 candidates in shared memory, builds the
-// candidate-by-candidate distance tile for every pair (earlier, chunk) with
-// FP32 direct differences (register-blocked 4x4 per thread), and one warp
-// scans the chunk in order: candidate c is occluded iff some kept s has
-// fmaf(alpha, d(s,c), -d(v,c)) <= 0 (one rounding, so the sign is that of
-// the exact alpha*d(s,c) - d(v,c)), decided with warp ballots.  The walk stops
-// once R candidates are kept.
+// For owner v with pool W: gather and deduplicate W (drop v and -1), order
+// the candidates by (d(v,c), id) and walk them: c is kept unless a kept s has
+// fmaf(alpha, d(s,c), -d(v,c)) <= 0 (one rounding, so the sign is that of the
+// exact alpha*d(s,c) - d(v,c)); the walk stops once R are kept.
+//
+// Every FP32 distance here is the same fixed chain, acc = fmaf(a_i - b_i,
+// a_i - b_i, acc) (or fmaf(a_i, b_i, acc), d = 1 - acc, for inner product)
+// over i = 0 .. dim-1 in order, whichever code path computes it.
+//
+// Fast path (pool <= kFastMax): the owner row and all candidate rows are
+// staged once in shared memory and one register-blocked pass builds the
+// owner distances and the whole candidate-by-candidate triangle; the
+// triangle then replaces the staged rows in the same buffer.  Slow path
+// (larger pools): owner distances first, then passes that stage the kept rows
+// plus the next 64 candidates.
 #include <float.h>
 
 #include "internal.h"
@@ -19,58 +24,114 @@ namespace rnsm {
 
 namespace {
 
-constexpr int kThreads = 128;
-constexpr int kTile = 64;       // candidates per pass
-constexpr int kDch = 128;       // dimensions staged per sub-pass
-constexpr int kStride = kDch + 4;  // staged row stride (floats): 33 float4, odd => no bank conflicts
-constexpr int kNB = 4;          // 4x4 pair blocks per thread (rows <= 128, chunk <= 64)
-constexpr int kPoolCapMax = 4096;  // larger pools set error bit 16
+constexpr int kThreads = 256;
+constexpr int kDch = 128;           // dimensions staged per sub-pass
+constexpr int kFastMax = 151;       // candidates of the one-tile path (rows = 1 + np <= 152)
+constexpr int kNBFMax = 3;          // 4x4 pair blocks per thread, fast path (152 rows)
+constexpr int kRowsNB1 = 88;        // rows whose triangle fits one block per thread
+constexpr int kTile = 64;           // candidates per slow-path pass
+constexpr int kNBS = 2;             // 4x4 pair blocks per thread, slow path
+constexpr int kPoolCapMax = 4096;   // larger pools set error bit 16
+
+// Staged row r starts at float4 index r*33 + (r >> 2): an odd stride plus a
+// one-float4 shift every 4 rows, so 8 threads reading the same column of
+// rows 4b+q (b = 0..7) hit 8 different bank groups.
+__device__ __forceinline__ int srow4(int r) { return r * (kDch / 4 + 1) + (r >> 2); }
+__host__ __device__ constexpr int rows_float4(int rows) { return rows * (kDch / 4 + 1) + rows / 4 + 1; }
+
+// Upper-triangle index of the pair (a, b), a < b, among n rows.
+__device__ __forceinline__ int tri(int a, int b, int n) { return a * (2 * n - a - 1) / 2 + (b - a - 1); }
 
 struct Smem {
-    float *rows;          // rows_cap * kStride
-    const float **rptr;   // rows_cap
-    float *tile;          // rows_cap * kTile
-    float *pd;            // pool_cap
-    int32_t *pid;         // pool_cap
-    int32_t *tmp;         // pool_cap
-    int32_t *krow;        // R
-    int32_t *kid;         // R
+    float4 *rows;          // staged rows; reused for the triangle
+    const float **rptr;    // row pointer of each staged row
+    float *pd;             // pool_cap: d(v, c)
+    int32_t *pid;          // pool_cap: candidate ids
+    int32_t *prow;         // pool_cap: staged row of each candidate (fast path)
+    int32_t *tmp;          // pool_cap
+    int32_t *krow;         // R: staged row of each kept candidate
+    int32_t *kid;          // R: kept ids in order
+    float *stile;          // slow path: rows_cap * kTile pair distances
 };
 
-size_t smem_bytes(int rows_cap, int pool_cap, int R) {
-    return (size_t)rows_cap * kStride * 4 + (size_t)rows_cap * sizeof(void *) +
-           (size_t)rows_cap * kTile * 4 + (size_t)pool_cap * 12 + (size_t)R * 8 + 64;
+size_t smem_bytes(int rows_cap, int pool_cap, int R, bool slow) {
+    size_t b = (size_t)rows_float4(rows_cap) * 16 + (size_t)rows_cap * sizeof(void *) +
+               (size_t)pool_cap * 16 + (size_t)R * 8 + 64;
+    if (slow) b += (size_t)rows_cap * kTile * 4;
+    return b;
 }
 
-__device__ __forceinline__ void carve(unsigned char *p, int rows_cap, int pool_cap, int R, Smem &s) {
-    s.rows = reinterpret_cast<float *>(p);
-    s.rptr = reinterpret_cast<const float **>(s.rows + (size_t)rows_cap * kStride);
-    s.tile = reinterpret_cast<float *>(s.rptr + rows_cap);
-    s.pd = s.tile + (size_t)rows_cap * kTile;
+__device__ __forceinline__ void carve(unsigned char *p, int rows_cap, int pool_cap, int R,
+                                      bool slow, Smem &s) {
+    s.rows = reinterpret_cast<float4 *>(p);
+    s.rptr = reinterpret_cast<const float **>(s.rows + rows_float4(rows_cap));
+    s.pd = reinterpret_cast<float *>(s.rptr + rows_cap);
     s.pid = reinterpret_cast<int32_t *>(s.pd + pool_cap);
-    s.tmp = s.pid + pool_cap;
+    s.prow = s.pid + pool_cap;
+    s.tmp = s.prow + pool_cap;
     s.krow = s.tmp + pool_cap;
     s.kid = s.krow + R;
+    s.stile = slow ? reinterpret_cast<float *>(s.kid + R) : nullptr;
 }
 
+__device__ __forceinline__ float chain(float acc, float4 a, float4 b, int metric) {
+    return metric == 0 ? l2_acc(acc, a, b) : ip_acc(acc, a, b);
+}
+
+// Stages float4 columns [d0/4, d0/4 + dc4) of rows [0, nrows4) (rptr) into smem.
+__device__ __forceinline__ void stage(const Smem &s, int nrows4, int d0, int dc4) {
+    for (int e = threadIdx.x; e < nrows4 * dc4; e += kThreads) {
+        const int r = e / dc4, f = e - r * dc4;
+        s.rows[srow4(r) + f] = ldg4(s.rptr[r] + d0 + 4 * f);
+    }
+}
+
+// Block bitonic sort of (pd, pid, prow) by (distance, id) over npad entries.
+__device__ void sort_pool(const Smem &s, int npad) {
+    const int tid = threadIdx.x;
+    for (int k = 2; k <= npad; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int x = tid; x < npad; x += kThreads) {
+                const int y = x ^ j;
+                if (y > x) {
+                    const bool up = (x & k) == 0;
+                    if (lex_less(s.pd[y], s.pid[y], s.pd[x], s.pid[x]) == up) {
+                        float td = s.pd[x]; s.pd[x] = s.pd[y]; s.pd[y] = td;
+                        int32_t ti = s.pid[x]; s.pid[x] = s.pid[y]; s.pid[y] = ti;
+                        ti = s.prow[x]; s.prow[x] = s.prow[y]; s.prow[y] = ti;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+template <int kNBF>
 __global__ void __launch_bounds__(kThreads) prune_kernel(const PruneArgs a, int rows_cap,
-                                                         int pool_cap, int chunk) {
+                                                         int pool_cap, int slow_ok, int chunk,
+                                                         const int32_t *idx_list,
+                                                         const unsigned long long *idx_count) {
     extern __shared__ __align__(16) unsigned char smem[];
     Smem s;
-    carve(smem, rows_cap, pool_cap, a.R, s);
+    carve(smem, rows_cap, pool_cap, a.R, slow_ok != 0, s);
     __shared__ int64_t sh_i;  // first owner of the claimed chunk
     __shared__ int sh_np, sh_nk, sh_ebase;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int dim = a.dim, F4 = dim >> 2;
     const int R = a.R;
+    const int metric = a.metric;
 
+    // owners: all of [0, n_owners), or the listed ones (pools the small-pool kernel passed on)
+    const int64_t n_items = idx_list ? (int64_t)*idx_count : a.n_owners;
     for (;;) {
         if (tid == 0) sh_i = atomicAdd(a.work, chunk);
         __syncthreads();
         const int64_t i0 = sh_i;
-        if (i0 >= a.n_owners) break;
-        const int64_t i1 = min(a.n_owners, i0 + chunk);
-      for (int64_t i = i0; i < i1; ++i) {
+        if (i0 >= n_items) break;
+        const int64_t i1 = min(n_items, i0 + chunk);
+      for (int64_t it = i0; it < i1; ++it) {
+        const int64_t i = idx_list ? (int64_t)idx_list[it] : it;
         const int32_t owner = a.owner_ids ? a.owner_ids[i] : (int32_t)(a.owner_base + i);
         int64_t c_lo = 0, c_hi = 0;
         if (a.csr_offs) {
@@ -103,7 +164,8 @@ __global__ void __launch_bounds__(kThreads) prune_kernel(const PruneArgs a, int 
         }
         if (tid == 0) sh_np = 0;
         __syncthreads();
-        // 2. Drop -1, the owner and duplicates (first occurrence survives).
+        // 2. Drop -1, the owner and duplicates (first occurrence survives);
+        //    the order of the survivors is irrelevant (they are sorted below).
         for (int j = tid; j < np_raw; j += kThreads) {
             const int32_t id = s.pid[j];
             bool ok = id >= 0 && id != owner;
@@ -113,176 +175,118 @@ __global__ void __launch_bounds__(kThreads) prune_kernel(const PruneArgs a, int 
         }
         __syncthreads();
         const int np = sh_np;
-        for (int j = tid; j < np; j += kThreads) s.pid[j] = s.tmp[j];
-        __syncthreads();
-
-        // 3. d(v, c) for every candidate: one warp per candidate, 4 at a time.
-        {
-            const float *orow = seg_row(a.segs, owner, dim);
-            for (int c0 = warp * 4; c0 < np; c0 += 16) {
-                const float *rw[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    rw[u] = c0 + u < np ? seg_row(a.segs, s.pid[c0 + u], dim) : orow;
-                float v[4] = {0.f, 0.f, 0.f, 0.f};
-                for (int f = lane; f < F4; f += 32) {
-                    const float4 o = ldg4(orow + 4 * f);
-                    float4 x[4];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) x[u] = ldg4(rw[u] + 4 * f);
-                    if (a.metric == 0) {
-#pragma unroll
-                        for (int u = 0; u < 4; ++u) v[u] = l2_acc(v[u], o, x[u]);
-                    } else {
-#pragma unroll
-                        for (int u = 0; u < 4; ++u) v[u] = ip_acc(v[u], o, x[u]);
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-#pragma unroll
-                    for (int off = 16; off > 0; off >>= 1)
-                        v[u] += __shfl_xor_sync(0xffffffffu, v[u], off);
-                }
-                if (lane == 0) {
-#pragma unroll
-                    for (int u = 0; u < 4; ++u)
-                        if (c0 + u < np) s.pd[c0 + u] = a.metric == 0 ? v[u] : 1.0f - v[u];
-                }
-            }
+        for (int j = tid; j < np; j += kThreads) {
+            s.pid[j] = s.tmp[j];
+            s.prow[j] = 1 + j;
         }
-        // 4. Sort (pd, pid) by (distance, id): bitonic over the next power of two.
         int npad = 1;
         while (npad < np) npad <<= 1;
         for (int j = np + tid; j < npad; j += kThreads) {
             s.pd[j] = INFINITY;
             s.pid[j] = INT32_MAX;
+            s.prow[j] = 0;
         }
         __syncthreads();
-        for (int k = 2; k <= npad; k <<= 1) {
-            for (int j = k >> 1; j > 0; j >>= 1) {
-                for (int x = tid; x < npad; x += kThreads) {
-                    const int y = x ^ j;
-                    if (y > x) {
-                        const bool up = (x & k) == 0;
-                        const bool gt = lex_less(s.pd[y], s.pid[y], s.pd[x], s.pid[x]);
-                        if (gt == up) {
-                            float td = s.pd[x]; s.pd[x] = s.pd[y]; s.pd[y] = td;
-                            int32_t ti = s.pid[x]; s.pid[x] = s.pid[y]; s.pid[y] = ti;
+
+        int nk = 0;
+        if (np <= kFastMax && 1 + np <= rows_cap) {
+            // ---------------- fast path: one tile over owner + pool ----------------
+            const int nrows = 1 + np;
+            const int nB = (nrows + 3) >> 2;
+            // a pool kept whole needs only the owner distances (block row 0)
+            const bool whole = a.keep_all_if_fit && np <= R;
+            const int nblk = whole ? nB : nB * (nB + 1) / 2;
+            for (int r = tid; r < 4 * nB; r += kThreads)
+                s.rptr[r] = seg_row(a.segs, r == 0 || r >= nrows ? owner : s.pid[r - 1], dim);
+            // this thread's blocks (ba <= bb), enumerated row by row
+            int bas[kNBF], bbs[kNBF];
+#pragma unroll
+            for (int t = 0; t < kNBF; ++t) {
+                int b = tid + kThreads * t, ba = 0;
+                if (b < nblk) {
+                    while (b >= nB - ba) { b -= nB - ba; ++ba; }
+                    bas[t] = ba;
+                    bbs[t] = ba + b;
+                } else {
+                    bas[t] = -1;
+                    bbs[t] = -1;
+                }
+            }
+            float acc[kNBF][4][4];
+#pragma unroll
+            for (int t = 0; t < kNBF; ++t)
+#pragma unroll
+                for (int p = 0; p < 4; ++p)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) acc[t][p][q] = 0.f;
+            __syncthreads();
+            for (int d0 = 0; d0 < dim; d0 += kDch) {
+                const int dc4 = min(kDch, dim - d0) >> 2;
+                stage(s, 4 * nB, d0, dc4);
+                __syncthreads();
+#pragma unroll
+                for (int t = 0; t < kNBF; ++t) {
+                    if (bas[t] < 0) continue;
+                    const float4 *ra = s.rows + srow4(4 * bas[t]);
+                    const float4 *rb = s.rows + srow4(4 * bbs[t]);
+                    for (int f = 0; f < dc4; ++f) {
+                        float4 xa[4], xb[4];
+#pragma unroll
+                        for (int p = 0; p < 4; ++p) {
+                            xa[p] = ra[p * (kDch / 4 + 1) + f];
+                            xb[p] = rb[p * (kDch / 4 + 1) + f];
                         }
+#pragma unroll
+                        for (int p = 0; p < 4; ++p)
+#pragma unroll
+                            for (int q = 0; q < 4; ++q)
+                                acc[t][p][q] = chain(acc[t][p][q], xa[p], xb[q], metric);
                     }
                 }
                 __syncthreads();
             }
-        }
-
-        // 5. Walk in order.
-        int nk = 0;
-        if (a.keep_all_if_fit && np <= R) {
-            for (int j = tid; j < np; j += kThreads) s.kid[j] = s.pid[j];
-            nk = np;
-        } else {
-            int pos = 0;
-            while (pos < np && nk < R) {
-                const int cs = min(kTile, np - pos);
-                const int nrows = nk + cs;
-                const int nA = (nrows + 3) >> 2, nB = (cs + 3) >> 2;
-                const int nblk = nA * nB;
-                // staged rows: kept [0, nk), chunk [nk, nrows)
-                for (int r = tid; r < nrows; r += kThreads) {
-                    const int32_t id = r < nk ? s.kid[r] : s.pid[pos + r - nk];
-                    s.rptr[r] = seg_row(a.segs, id, dim);
-                }
-                for (int r = nrows + tid; r < 4 * nA; r += kThreads)
-                    s.rptr[r] = seg_row(a.segs, owner, dim);  // padding rows: any valid row
-                for (int j = tid; j < nk; j += kThreads) s.krow[j] = j;
-                __syncthreads();
-                float acc[kNB][4][4];
+            // the triangle replaces the staged rows
+            float *T = reinterpret_cast<float *>(s.rows);
 #pragma unroll
-                for (int t = 0; t < kNB; ++t)
+            for (int t = 0; t < kNBF; ++t) {
+                if (bas[t] < 0) continue;
 #pragma unroll
-                    for (int p = 0; p < 4; ++p)
+                for (int p = 0; p < 4; ++p)
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) acc[t][p][q] = 0.f;
-                for (int d0 = 0; d0 < dim; d0 += kDch) {
-                    const int dc4 = min(kDch, dim - d0) >> 2;
-                    const int rows4 = 4 * nA;
-                    for (int e = tid; e < rows4 * dc4; e += kThreads) {
-                        const int r = e / dc4, f = e - r * dc4;
-                        const float4 v = ldg4(s.rptr[r] + d0 + 4 * f);
-                        *reinterpret_cast<float4 *>(s.rows + (size_t)r * kStride + 4 * f) = v;
+                    for (int q = 0; q < 4; ++q) {
+                        const int ra = 4 * bas[t] + p, rb = 4 * bbs[t] + q;
+                        if (ra < rb && rb < nrows)
+                            T[tri(ra, rb, nrows)] = metric == 0 ? acc[t][p][q] : 1.0f - acc[t][p][q];
                     }
-                    __syncthreads();
-#pragma unroll
-                    for (int t = 0; t < kNB; ++t) {
-                        const int b = tid + kThreads * t;
-                        if (b < nblk) {
-                            const int ba = b / nB, bb = b - ba * nB;
-                            const float *ra[4], *rb[4];
-#pragma unroll
-                            for (int p = 0; p < 4; ++p) {
-                                ra[p] = s.rows + (size_t)(ba + nA * p) * kStride;
-                                int rbi = nk + bb + nB * p;
-                                if (rbi >= 4 * nA) rbi = 0;
-                                rb[p] = s.rows + (size_t)rbi * kStride;
-                            }
-                            for (int f = 0; f < dc4; ++f) {
-                                float4 xa[4], xb[4];
-#pragma unroll
-                                for (int p = 0; p < 4; ++p) {
-                                    xa[p] = *reinterpret_cast<const float4 *>(ra[p] + 4 * f);
-                                    xb[p] = *reinterpret_cast<const float4 *>(rb[p] + 4 * f);
-                                }
-                                if (a.metric == 0) {
-#pragma unroll
-                                    for (int p = 0; p < 4; ++p)
-#pragma unroll
-                                        for (int q = 0; q < 4; ++q)
-                                            acc[t][p][q] = l2_acc(acc[t][p][q], xa[p], xb[q]);
-                                } else {
-#pragma unroll
-                                    for (int p = 0; p < 4; ++p)
-#pragma unroll
-                                        for (int q = 0; q < 4; ++q)
-                                            acc[t][p][q] = ip_acc(acc[t][p][q], xa[p], xb[q]);
-                                }
-                            }
-                        }
-                    }
-                    __syncthreads();
-                }
-#pragma unroll
-                for (int t = 0; t < kNB; ++t) {
-                    const int b = tid + kThreads * t;
-                    if (b < nblk) {
-                        const int ba = b / nB, bb = b - ba * nB;
-#pragma unroll
-                        for (int p = 0; p < 4; ++p)
-#pragma unroll
-                            for (int q = 0; q < 4; ++q) {
-                                const int ar = ba + nA * p, bc = bb + nB * q;
-                                if (ar < nrows && bc < cs && ar < nk + bc)
-                                    s.tile[ar * kTile + bc] =
-                                        a.metric == 0 ? acc[t][p][q] : 1.0f - acc[t][p][q];
-                            }
-                    }
-                }
-                __syncthreads();
+            }
+            __syncthreads();
+            for (int j = tid; j < np; j += kThreads) s.pd[j] = T[tri(0, 1 + j, nrows)];
+            __syncthreads();
+            sort_pool(s, npad);
+            if (a.keep_all_if_fit && np <= R) {
+                for (int j = tid; j < np; j += kThreads) s.kid[j] = s.pid[j];
+                nk = np;
+            } else {
                 if (warp == 0) {
-                    int nkk = nk;
-                    for (int bc = 0; bc < cs && nkk < R; ++bc) {
-                        const float dvc = s.pd[pos + bc];
+                    int nkk = 0;
+                    for (int c = 0; c < np && nkk < R; ++c) {
+                        const float dvc = s.pd[c];
+                        const int cr = s.prow[c];
                         bool occ = false;
                         for (int j0 = 0; j0 < nkk && !occ; j0 += 32) {
                             const int j = j0 + lane;
                             bool t = false;
-                            if (j < nkk) t = fmaf(a.alpha, s.tile[s.krow[j] * kTile + bc], -dvc) <= 0.f;
+                            if (j < nkk) {
+                                const int kr = s.krow[j];
+                                const float dsc = kr < cr ? T[tri(kr, cr, nrows)] : T[tri(cr, kr, nrows)];
+                                t = fmaf(a.alpha, dsc, -dvc) <= 0.f;
+                            }
                             occ = __any_sync(0xffffffffu, t);
                         }
                         if (!occ) {
                             if (lane == 0) {
-                                s.krow[nkk] = nk + bc;
-                                s.kid[nkk] = s.pid[pos + bc];
+                                s.krow[nkk] = cr;
+                                s.kid[nkk] = s.pid[c];
                             }
                             ++nkk;
                             __syncwarp();
@@ -292,12 +296,123 @@ __global__ void __launch_bounds__(kThreads) prune_kernel(const PruneArgs a, int 
                 }
                 __syncthreads();
                 nk = sh_nk;
-                pos += cs;
+            }
+        } else {
+            // ---------------- slow path: large pools ----------------
+            // d(v, c): one thread per candidate, the same chain from global memory
+            const float *orow = seg_row(a.segs, owner, dim);
+            for (int j = tid; j < np; j += kThreads) {
+                const float *row = seg_row(a.segs, s.pid[j], dim);
+                float acc = 0.f;
+                for (int f = 0; f < F4; ++f) acc = chain(acc, ldg4(orow + 4 * f), ldg4(row + 4 * f), metric);
+                s.pd[j] = metric == 0 ? acc : 1.0f - acc;
+            }
+            __syncthreads();
+            sort_pool(s, npad);
+            if (a.keep_all_if_fit && np <= R) {
+                for (int j = tid; j < np; j += kThreads) s.kid[j] = s.pid[j];
+                nk = np;
+            } else {
+                int pos = 0;
+                while (pos < np && nk < R) {
+                    const int cs = min(kTile, np - pos);
+                    const int nrows = nk + cs;  // kept [0, nk), chunk [nk, nrows)
+                    const int nA = (nrows + 3) >> 2, nB = (cs + 3) >> 2;
+                    const int nblk = nA * nB;
+                    for (int r = tid; r < 4 * nA; r += kThreads) {
+                        const int32_t id = r < nk ? s.kid[r] : (r < nrows ? s.pid[pos + r - nk] : owner);
+                        s.rptr[r] = seg_row(a.segs, id, dim);
+                    }
+                    for (int j = tid; j < nk; j += kThreads) s.krow[j] = j;
+                    __syncthreads();
+                    float acc[kNBS][4][4];
+#pragma unroll
+                    for (int t = 0; t < kNBS; ++t)
+#pragma unroll
+                        for (int p = 0; p < 4; ++p)
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) acc[t][p][q] = 0.f;
+                    for (int d0 = 0; d0 < dim; d0 += kDch) {
+                        const int dc4 = min(kDch, dim - d0) >> 2;
+                        stage(s, 4 * nA, d0, dc4);
+                        __syncthreads();
+#pragma unroll
+                        for (int t = 0; t < kNBS; ++t) {
+                            const int b = tid + kThreads * t;
+                            if (b >= nblk) continue;
+                            const int ba = b / nB, bb = b - ba * nB;
+                            const float4 *ra[4], *rb[4];
+#pragma unroll
+                            for (int p = 0; p < 4; ++p) {
+                                ra[p] = s.rows + srow4(ba + nA * p);
+                                int rbi = nk + bb + nB * p;
+                                if (rbi >= 4 * nA) rbi = 0;
+                                rb[p] = s.rows + srow4(rbi);
+                            }
+                            for (int f = 0; f < dc4; ++f) {
+                                float4 xa[4], xb[4];
+#pragma unroll
+                                for (int p = 0; p < 4; ++p) {
+                                    xa[p] = ra[p][f];
+                                    xb[p] = rb[p][f];
+                                }
+#pragma unroll
+                                for (int p = 0; p < 4; ++p)
+#pragma unroll
+                                    for (int q = 0; q < 4; ++q)
+                                        acc[t][p][q] = chain(acc[t][p][q], xa[p], xb[q], metric);
+                            }
+                        }
+                        __syncthreads();
+                    }
+#pragma unroll
+                    for (int t = 0; t < kNBS; ++t) {
+                        const int b = tid + kThreads * t;
+                        if (b >= nblk) continue;
+                        const int ba = b / nB, bb = b - ba * nB;
+#pragma unroll
+                        for (int p = 0; p < 4; ++p)
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) {
+                                const int ar = ba + nA * p, bc = bb + nB * q;
+                                if (ar < nrows && bc < cs && ar < nk + bc)
+                                    s.stile[ar * kTile + bc] =
+                                        metric == 0 ? acc[t][p][q] : 1.0f - acc[t][p][q];
+                            }
+                    }
+                    __syncthreads();
+                    if (warp == 0) {
+                        int nkk = nk;
+                        for (int bc = 0; bc < cs && nkk < R; ++bc) {
+                            const float dvc = s.pd[pos + bc];
+                            bool occ = false;
+                            for (int j0 = 0; j0 < nkk && !occ; j0 += 32) {
+                                const int j = j0 + lane;
+                                bool t = false;
+                                if (j < nkk)
+                                    t = fmaf(a.alpha, s.stile[s.krow[j] * kTile + bc], -dvc) <= 0.f;
+                                occ = __any_sync(0xffffffffu, t);
+                            }
+                            if (!occ) {
+                                if (lane == 0) {
+                                    s.krow[nkk] = nk + bc;
+                                    s.kid[nkk] = s.pid[pos + bc];
+                                }
+                                ++nkk;
+                                __syncwarp();
+                            }
+                        }
+                        if (lane == 0) sh_nk = nkk;
+                    }
+                    __syncthreads();
+                    nk = sh_nk;
+                    pos += cs;
+                }
             }
         }
         __syncthreads();
 
-        // 6. Output and reverse-edge emission.
+        // Output and reverse-edge emission.
         int32_t *orow = a.out + (a.out_by_index ? i : (int64_t)owner) * R;
         for (int j = tid; j < R; j += kThreads) orow[j] = j < nk ? s.kid[j] : -1;
         if (a.eu && warp == 0) {
@@ -328,33 +443,341 @@ __global__ void __launch_bounds__(kThreads) prune_kernel(const PruneArgs a, int 
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// Small pools (at most 64 raw candidates: the source pool list(v) + c_cross
+// results and most target pools).  128 threads, about 38 KB of shared memory:
+// the owner row and every raw candidate row are staged once, one register-
+// blocked pass builds the triangle of all pairwise distances (row 0 = the
+// owner), and warp 0 sorts the candidates by (d(v,c), id) in registers,
+// drops the owner, -1 and duplicates (equal ids sort next to each other) and
+// scans.  Larger pools are appended to an overflow list for prune_kernel.
+
+constexpr int kSmallThreads = 128;
+constexpr int kSmallMax = 64;
+constexpr int kSmallRows = 68;      // owner + 64, rounded up to 4
+constexpr int kSmallNB = 2;         // 17*18/2 = 153 blocks over 128 threads
+
+// Ascending bitonic sort of 64 (d, id, r) triples, element e = lane + 32*h.
+__device__ __forceinline__ void warp_sort64(float (&d)[2], int32_t (&id)[2], int32_t (&r)[2]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 2; k <= 64; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j == 32) {  // partner is the lane's other element; k == 64: ascending
+                if (lex_less(d[1], id[1], d[0], id[0])) {
+                    float td = d[0]; d[0] = d[1]; d[1] = td;
+                    int32_t ti = id[0]; id[0] = id[1]; id[1] = ti;
+                    ti = r[0]; r[0] = r[1]; r[1] = ti;
+                }
+                continue;
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int e = lane + 32 * h;
+                const float od = __shfl_xor_sync(0xffffffffu, d[h], j);
+                const int32_t oi = __shfl_xor_sync(0xffffffffu, id[h], j);
+                const int32_t orr = __shfl_xor_sync(0xffffffffu, r[h], j);
+                const bool up = (e & k) == 0;
+                const bool lower = (lane & j) == 0;
+                const bool take = (lower == up) ? lex_less(od, oi, d[h], id[h])
+                                                : lex_less(d[h], id[h], od, oi);
+                if (take) { d[h] = od; id[h] = oi; r[h] = orr; }
+            }
+        }
+    }
+}
+
+struct SmallSmem {
+    float4 rows[rows_float4(kSmallRows)];
+    const float *rptr[kSmallRows];
+    int32_t pid[kSmallMax];
+    float sd[kSmallMax];
+    int32_t sid[kSmallMax];
+    int32_t srow[kSmallMax];
+    int32_t kid[kSmallMax];
+    int32_t krow[kSmallMax];
+};
+
+__global__ void __launch_bounds__(kSmallThreads) prune_small_kernel(const PruneArgs a, int chunk) {
+    __shared__ __align__(16) SmallSmem s;
+    __shared__ int64_t sh_i;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int dim = a.dim;
+    const int R = a.R;
+    const int metric = a.metric;
+    for (;;) {
+        if (tid == 0) sh_i = atomicAdd(a.work, chunk);
+        __syncthreads();
+        const int64_t i0 = sh_i;
+        if (i0 >= a.n_owners) break;
+        const int64_t i1 = min(a.n_owners, i0 + chunk);
+      for (int64_t i = i0; i < i1; ++i) {
+        const int32_t owner = a.owner_ids ? a.owner_ids[i] : (int32_t)(a.owner_base + i);
+        int64_t c_lo = 0, c_hi = 0;
+        if (a.csr_offs) {
+            c_lo = a.csr_offs[i];
+            c_hi = a.csr_offs[i + 1];
+        }
+        if (a.skip_empty_csr && c_hi == c_lo) continue;   // uniform: no shared state touched
+        const int64_t nr_raw = (int64_t)a.lenA + a.lenB + (c_hi - c_lo);
+        if (nr_raw > kSmallMax) {
+            if (tid == 0) a.ovf_list[atomicAdd(a.ovf_count, 1ull)] = (int32_t)i;
+            continue;
+        }
+        const int nr = (int)nr_raw;
+        const float *orow = seg_row(a.segs, owner, dim);
+        for (int j = tid; j < kSmallMax; j += kSmallThreads) {
+            int32_t id = -1;
+            if (j < nr) {
+                if (j < a.lenA) {
+                    id = a.listA[(int64_t)owner * a.lenA + j];
+                } else if (j < a.lenA + a.lenB) {
+                    id = a.listB[i * a.strideB + (j - a.lenA)];
+                    if (id >= 0) id += a.offB;
+                } else {
+                    id = a.csr_ids[c_lo + (j - a.lenA - a.lenB)];
+                }
+                if (id == owner) id = -1;
+            }
+            s.pid[j] = id;
+            s.rptr[1 + j] = id >= 0 ? seg_row(a.segs, id, dim) : orow;
+        }
+        for (int r = kSmallMax + 1 + tid; r < kSmallRows; r += kSmallThreads) s.rptr[r] = orow;
+        if (tid == 0) s.rptr[0] = orow;
+        __syncthreads();
+
+        const bool whole = a.keep_all_if_fit && nr <= R;
+        const int nrows = 1 + nr;
+        const int nB = (nrows + 3) >> 2;
+        const int nblk = whole ? nB : nB * (nB + 1) / 2;
+        int bas[kSmallNB], bbs[kSmallNB];
+#pragma unroll
+        for (int t = 0; t < kSmallNB; ++t) {
+            int b = tid + kSmallThreads * t, ba = 0;
+            if (b < nblk) {
+                while (b >= nB - ba) { b -= nB - ba; ++ba; }
+                bas[t] = ba;
+                bbs[t] = ba + b;
+            } else {
+                bas[t] = -1;
+                bbs[t] = -1;
+            }
+        }
+        float acc[kSmallNB][4][4];
+#pragma unroll
+        for (int t = 0; t < kSmallNB; ++t)
+#pragma unroll
+            for (int p = 0; p < 4; ++p)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[t][p][q] = 0.f;
+        for (int d0 = 0; d0 < dim; d0 += kDch) {
+            const int dc4 = min(kDch, dim - d0) >> 2;
+            for (int e = tid; e < 4 * nB * dc4; e += kSmallThreads) {
+                const int r = e / dc4, f = e - r * dc4;
+                s.rows[srow4(r) + f] = ldg4(s.rptr[r] + d0 + 4 * f);
+            }
+            __syncthreads();
+#pragma unroll
+            for (int t = 0; t < kSmallNB; ++t) {
+                if (bas[t] < 0) continue;
+                const float4 *ra = s.rows + srow4(4 * bas[t]);
+                const float4 *rb = s.rows + srow4(4 * bbs[t]);
+                for (int f = 0; f < dc4; ++f) {
+                    float4 xa[4], xb[4];
+#pragma unroll
+                    for (int p = 0; p < 4; ++p) {
+                        xa[p] = ra[p * (kDch / 4 + 1) + f];
+                        xb[p] = rb[p * (kDch / 4 + 1) + f];
+                    }
+#pragma unroll
+                    for (int p = 0; p < 4; ++p)
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            acc[t][p][q] = chain(acc[t][p][q], xa[p], xb[q], metric);
+                }
+            }
+            __syncthreads();
+        }
+        float *T = reinterpret_cast<float *>(s.rows);
+#pragma unroll
+        for (int t = 0; t < kSmallNB; ++t) {
+            if (bas[t] < 0) continue;
+#pragma unroll
+            for (int p = 0; p < 4; ++p)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int ra = 4 * bas[t] + p, rb = 4 * bbs[t] + q;
+                    if (ra < rb && rb < nrows)
+                        T[tri(ra, rb, nrows)] = metric == 0 ? acc[t][p][q] : 1.0f - acc[t][p][q];
+                }
+        }
+        __syncthreads();
+
+        if (warp == 0) {
+            float d[2];
+            int32_t id[2], rr[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int e = lane + 32 * h;
+                const bool valid = e < nr && s.pid[e] >= 0;
+                d[h] = valid ? T[tri(0, 1 + e, nrows)] : INFINITY;
+                id[h] = valid ? s.pid[e] : INT32_MAX;
+                rr[h] = 1 + e;
+            }
+            warp_sort64(d, id, rr);
+            // unique candidates in order: element e keeps if valid and its id
+            // differs from element e-1's (duplicates share (d, id), so they sit together)
+            const int32_t prev0 = __shfl_up_sync(0xffffffffu, id[0], 1);
+            const int32_t last0 = __shfl_sync(0xffffffffu, id[0], 31);
+            const int32_t prev1 = __shfl_up_sync(0xffffffffu, id[1], 1);
+            const bool k0 = id[0] != INT32_MAX && !(lane > 0 && prev0 == id[0]);
+            const bool k1 = id[1] != INT32_MAX && !(lane > 0 ? prev1 == id[1] : last0 == id[1]);
+            const unsigned m0 = __ballot_sync(0xffffffffu, k0);
+            const unsigned m1 = __ballot_sync(0xffffffffu, k1);
+            const int c0 = __popc(m0);
+            const int np = c0 + __popc(m1);
+            if (k0) {
+                const int p = __popc(m0 & lanemask_lt());
+                s.sd[p] = d[0]; s.sid[p] = id[0]; s.srow[p] = rr[0];
+            }
+            if (k1) {
+                const int p = c0 + __popc(m1 & lanemask_lt());
+                s.sd[p] = d[1]; s.sid[p] = id[1]; s.srow[p] = rr[1];
+            }
+            __syncwarp();
+            int nk = 0;
+            if (a.keep_all_if_fit && np <= R) {
+                for (int j = lane; j < np; j += 32) s.kid[j] = s.sid[j];
+                nk = np;
+            } else {
+                for (int c = 0; c < np && nk < R; ++c) {
+                    const float dvc = s.sd[c];
+                    const int cr = s.srow[c];
+                    bool occ = false;
+                    for (int j0 = 0; j0 < nk && !occ; j0 += 32) {
+                        const int j = j0 + lane;
+                        bool t = false;
+                        if (j < nk) {
+                            const int kr = s.krow[j];
+                            const float dsc = kr < cr ? T[tri(kr, cr, nrows)] : T[tri(cr, kr, nrows)];
+                            t = fmaf(a.alpha, dsc, -dvc) <= 0.f;
+                        }
+                        occ = __any_sync(0xffffffffu, t);
+                    }
+                    if (!occ) {
+                        if (lane == 0) {
+                            s.krow[nk] = cr;
+                            s.kid[nk] = s.sid[c];
+                        }
+                        ++nk;
+                        __syncwarp();
+                    }
+                }
+            }
+            __syncwarp();
+            int32_t *out = a.out + (a.out_by_index ? i : (int64_t)owner) * R;
+            for (int j = lane; j < R; j += 32) out[j] = j < nk ? s.kid[j] : -1;
+            if (a.eu) {
+                int done = 0;
+                int base = 0;
+                int cnt = 0;
+                for (int j0 = 0; j0 < nk; j0 += 32) {
+                    const int j = j0 + lane;
+                    cnt += __popc(__ballot_sync(0xffffffffu, j < nk && s.kid[j] >= a.emit_lo &&
+                                                                 s.kid[j] < a.emit_hi));
+                }
+                if (lane == 0 && cnt) base = (int)atomicAdd(a.ecount, (unsigned long long)cnt);
+                base = __shfl_sync(0xffffffffu, base, 0);
+                for (int j0 = 0; j0 < nk; j0 += 32) {
+                    const int j = j0 + lane;
+                    const bool e = j < nk && s.kid[j] >= a.emit_lo && s.kid[j] < a.emit_hi;
+                    const unsigned m = __ballot_sync(0xffffffffu, e);
+                    if (e) {
+                        const int slot = base + done + __popc(m & lanemask_lt());
+                        a.eu[slot] = s.kid[j];
+                        a.ev[slot] = owner;
+                    }
+                    done += __popc(m);
+                }
+            }
+        }
+        __syncthreads();
+      }
+        __syncthreads();  // every thread has read sh_i before it is claimed again
+    }
+}
+
+}  // namespace
+
+namespace {
+
+cudaError_t launch_general(const PruneArgs &a, const int32_t *idx_list,
+                           const unsigned long long *idx_count, cudaStream_t st) {
+    const int64_t maxpool = (int64_t)a.lenA + a.lenB + (a.csr_offs ? a.csr_max : 0);
+    int pool_cap = 64;
+    while (pool_cap < maxpool && pool_cap < kPoolCapMax) pool_cap <<= 1;
+    const bool slow = maxpool > kFastMax;
+    const int fast_rows = 4 * (int)((std::min<int64_t>(maxpool, kFastMax) + 1 + 3) / 4);
+    const int slow_rows = 4 * ((a.R + kTile + 3) / 4);
+    const int rows_cap = slow ? std::max(fast_rows, slow_rows) : fast_rows;
+    const size_t smem = smem_bytes(rows_cap, pool_cap, a.R, slow);
+    auto kern = fast_rows <= kRowsNB1 ? prune_kernel<1> : prune_kernel<kNBFMax>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    int64_t grid = (int64_t)sms * per_sm;
+    // Sparse passes (most owners without CSR entries) claim owners 32 at a time.
+    const int chunk = a.skip_empty_csr && !idx_list ? 32 : 1;
+    if (!idx_list) {
+        const int64_t want = (a.n_owners + chunk - 1) / chunk;
+        if (want < grid) grid = want;
+    }
+    kern<<<(unsigned)grid, kThreads, smem, st>>>(a, rows_cap, pool_cap, slow ? 1 : 0, chunk,
+                                                 idx_list, idx_count);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t launch_prune(const PruneArgs &a, cudaStream_t st) {
     if (a.n_owners <= 0) return cudaSuccess;
     if (a.R > 64 || a.dim > 1024 || (a.dim & 3)) return cudaErrorInvalidValue;
-    const int64_t maxpool = (int64_t)a.lenA + a.lenB + (a.csr_offs ? a.csr_max : 0);
-    int pool_cap = 64;
-    while (pool_cap < maxpool && pool_cap < kPoolCapMax) pool_cap <<= 1;
-    const int rows_cap = ((a.R + kTile + 3) / 4) * 4;
-    const size_t smem = smem_bytes(rows_cap, pool_cap, a.R);
-    cudaError_t e = cudaFuncSetAttribute(prune_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    const bool small_ok = a.ovf_list && a.ovf_count && a.work2 && a.lenA + a.lenB <= kSmallMax;
+    if (!small_ok) return launch_general(a, nullptr, nullptr, st);
+    cudaError_t e = cudaMemsetAsync(a.ovf_count, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
+    cudaFuncSetAttribute(prune_small_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, prune_kernel, kThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, prune_small_kernel, kSmallThreads, 0);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
-    int64_t grid = (int64_t)sms * per_sm;
-    // Sparse passes (most owners without CSR entries) claim owners 32 at a time.
     const int chunk = a.skip_empty_csr ? 32 : 1;
-    int64_t want = (a.n_owners + chunk - 1) / chunk;
+    int64_t grid = (int64_t)sms * per_sm;
+    const int64_t want = (a.n_owners + chunk - 1) / chunk;
     if (want < grid) grid = want;
-    prune_kernel<<<(unsigned)grid, kThreads, smem, st>>>(a, rows_cap, pool_cap, chunk);
+    prune_small_kernel<<<(unsigned)grid, kSmallThreads, 0, st>>>(a, chunk);
     note_launches(1);
-    return cudaGetLastError();
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (a.lenA + a.lenB + (a.csr_offs ? a.csr_max : 0) <= kSmallMax) return cudaSuccess;
+    // owners whose pools exceeded 64 raw candidates (the count stays on the device)
+    PruneArgs b = a;
+    b.work = a.work2;
+    e = cudaMemsetAsync(b.work, 0, sizeof(int32_t), st);
+    if (e != cudaSuccess) return e;
+    return launch_general(b, a.ovf_list, a.ovf_count, st);
 }
 
 }  // namespace rnsm
