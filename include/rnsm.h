@@ -259,6 +259,32 @@ RNSM_API rnsm_status rnsm_prune(const float *vecs, int64_t n, int32_t dim, const
                        void *stream);
 
 /*
+ * rnsm_prune_noalloc -- rnsm_prune (FP32) that allocates no device memory.
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that cannot let a library allocate: services that give all device memory
+ * to their own pool allocator up front and leave no headroom for a
+ * library's cudaMalloc, and latency-critical paths that cannot afford the
+ * device-wide synchronisation that cudaMalloc and cudaFree may imply.
+ * Its scratch (work counters, error word, a list of owners with pools over
+ * 64 candidates) is a static device array of 256 B + 4 B per owner for
+ * RNSM_PRUNE_NOALLOC_MAX_OWNERS owners (1 MiB), held by every device that
+ * loads the library until the process exits.
+ *   Arguments, layout and results as rnsm_prune (prec is always FP32).
+ *   nv > RNSM_PRUNE_NOALLOC_MAX_OWNERS gives RNSM_EINVAL.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  Every call on a device shares the one array
+ * (each call clears its counters first): calls that overlap on the GPU, from
+ * several host threads or streams, race and must be serialised by the
+ * caller.
+ */
+#define RNSM_PRUNE_NOALLOC_MAX_OWNERS 262144
+RNSM_API rnsm_status rnsm_prune_noalloc(const float *vecs, int64_t n, int32_t dim,
+                                        const int32_t *owners, int64_t nv, const int32_t *pool,
+                                        int32_t w_len, int32_t R, float alpha, int32_t metric,
+                                        int32_t keep_all_if_fit, int32_t *out, void *stream);
+
+/*
  * rnsm_reverse_edges -- the target side of UpdateGraph (Section 4.2): target
  * vertices gain cross edges only through the reverse edges of the kept
  * source edges.  Edges (u <- v) are grouped by u with a counting sort

@@ -277,6 +277,8 @@ rnsm_status reverse_into(const SegTable &tab, int32_t dim, const rnsm_params &p,
 
 }  // namespace
 
+void rnsm::set_last_error(const char *msg) { g_err = msg; }
+
 // ======================================================================= ABI
 
 extern "C" {

@@ -8,6 +8,9 @@
 
 namespace rnsm {
 
+// Sets the calling thread's rnsm_last_error() message.
+void set_last_error(const char *msg);
+
 // Kernels launched by this library (every launcher adds its count).
 void note_launches(int n);
 long long launches_so_far();

@@ -80,6 +80,7 @@ _SIGS = {
     "rnsm_select_pivots_gpu": (i32, [P, i64, i32, i32, P, P, P, P, P, P]),
     "rnsm_prune": (i32, [P, i64, i32, P, i64, P, i32, i32, f32, i32, i32, i32, P, P]),
     "rnsm_reverse_edges": (i32, [P, i64, i32, P, i32, P, P, i64, f32, i32, P]),
+    "rnsm_prune_noalloc": (i32, [P, i64, i32, P, i64, P, i32, i32, f32, i32, i32, P, P]),
     "rnsm_build_segment": (i32, [P, i64, i32, P, i64, P, P, P]),
     "rnsm_medoid": (i32, [P, i64, i32, i32, P, P]),
     "rnsm_last_error": (C.c_char_p, []),
@@ -262,6 +263,23 @@ def prune(vecs, owners, pool, R, alpha, metric=L2, keep_all_if_fit=False, prec=F
                             _dev(owners, torch.int32, "owners"), nv,
                             _dev(pool, torch.int32, "pool"), pool.shape[1], R, alpha, metric,
                             int(keep_all_if_fit), prec, C.c_void_p(out.data_ptr()), _stream()))
+    return out
+
+
+NOALLOC_MAX_OWNERS = 262144
+
+
+def prune_noalloc(vecs, owners, pool, R, alpha, metric=L2, keep_all_if_fit=False, out=None):
+    """rnsm_prune without device allocation inside the library (the caller
+    provides ``out``; scratch is the library's static device array)."""
+    nv = owners.shape[0]
+    if out is None:
+        out = torch.empty((nv, R), dtype=torch.int32, device=vecs.device)
+    _check(lib().rnsm_prune_noalloc(_dev(vecs, torch.float32, "vecs"), vecs.shape[0],
+                                    vecs.shape[1], _dev(owners, torch.int32, "owners"), nv,
+                                    _dev(pool, torch.int32, "pool"), pool.shape[1], R, alpha,
+                                    metric, int(keep_all_if_fit), _dev(out, torch.int32, "out"),
+                                    _stream()))
     return out
 
 
