@@ -449,55 +449,27 @@ __global__ void __launch_bounds__(kThreads) prune_kernel(const PruneArgs a, int 
 // results and most target pools).  128 threads, about 38 KB of shared memory:
 // the owner row and every raw candidate row are staged once, one register-
 // blocked pass builds the triangle of all pairwise distances (row 0 = the
-// owner), and warp 0 sorts the candidates by (d(v,c), id) in registers,
-// drops the owner, -1 and duplicates (equal ids sort next to each other) and
-// scans.  Larger pools are appended to an overflow list for prune_kernel.
+// owner), all threads rank the candidates by (d(v,c), id) and build, for
+// every candidate, the bitmask of earlier candidates that would occlude it;
+// the greedy walk is then a loop over 64-bit masks.  The owner, -1 and
+// duplicates (equal keys rank next to each other) are skipped.  Larger pools
+// are appended to an overflow list for prune_kernel.
 
 constexpr int kSmallThreads = 128;
 constexpr int kSmallMax = 64;
 constexpr int kSmallRows = 68;      // owner + 64, rounded up to 4
 constexpr int kSmallNB = 2;         // 17*18/2 = 153 blocks over 128 threads
 
-// Ascending bitonic sort of 64 (d, id, r) triples, element e = lane + 32*h.
-__device__ __forceinline__ void warp_sort64(float (&d)[2], int32_t (&id)[2], int32_t (&r)[2]) {
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int k = 2; k <= 64; k <<= 1) {
-#pragma unroll
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            if (j == 32) {  // partner is the lane's other element; k == 64: ascending
-                if (lex_less(d[1], id[1], d[0], id[0])) {
-                    float td = d[0]; d[0] = d[1]; d[1] = td;
-                    int32_t ti = id[0]; id[0] = id[1]; id[1] = ti;
-                    ti = r[0]; r[0] = r[1]; r[1] = ti;
-                }
-                continue;
-            }
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int e = lane + 32 * h;
-                const float od = __shfl_xor_sync(0xffffffffu, d[h], j);
-                const int32_t oi = __shfl_xor_sync(0xffffffffu, id[h], j);
-                const int32_t orr = __shfl_xor_sync(0xffffffffu, r[h], j);
-                const bool up = (e & k) == 0;
-                const bool lower = (lane & j) == 0;
-                const bool take = (lower == up) ? lex_less(od, oi, d[h], id[h])
-                                                : lex_less(d[h], id[h], od, oi);
-                if (take) { d[h] = od; id[h] = oi; r[h] = orr; }
-            }
-        }
-    }
-}
-
 struct SmallSmem {
     float4 rows[rows_float4(kSmallRows)];
     const float *rptr[kSmallRows];
     int32_t pid[kSmallMax];
-    float sd[kSmallMax];
+    float kd[kSmallMax];       // raw keys
+    int32_t kix[kSmallMax];
+    float sd[kSmallMax];       // keys in (distance, id) order
     int32_t sid[kSmallMax];
-    int32_t srow[kSmallMax];
-    int32_t kid[kSmallMax];
-    int32_t krow[kSmallMax];
+    int32_t srow[kSmallMax];   // staged row of each ordered entry
+    uint32_t occ[2 * kSmallMax];
 };
 
 __global__ void __launch_bounds__(kSmallThreads) prune_small_kernel(const PruneArgs a, int chunk) {
@@ -615,91 +587,106 @@ __global__ void __launch_bounds__(kSmallThreads) prune_small_kernel(const PruneA
         }
         __syncthreads();
 
+        // Order: every raw entry's rank by (d(v,c), id), counted by all
+        // threads; duplicates (equal keys) rank by raw index, so they land
+        // next to each other; -1 and the owner sort last.
+        for (int j = tid; j < kSmallMax; j += kSmallThreads) {
+            const bool valid = j < nr && s.pid[j] >= 0;
+            s.kd[j] = valid ? T[tri(0, 1 + j, nrows)] : INFINITY;
+            s.kix[j] = valid ? s.pid[j] : INT32_MAX;
+        }
+        __syncthreads();
+        for (int j = tid; j < nr; j += kSmallThreads) {
+            const float dj = s.kd[j];
+            const int32_t ij = s.kix[j];
+            int r = 0;
+            for (int k = 0; k < nr; ++k) {
+                const float dk = s.kd[k];
+                const int32_t ik = s.kix[k];
+                r += lex_less(dk, ik, dj, ij) || (dk == dj && ik == ij && k < j);
+            }
+            s.sd[r] = dj;
+            s.sid[r] = ij;
+            s.srow[r] = 1 + j;
+        }
+        __syncthreads();
+        // Occluders of every candidate, in parallel: bit s of occ[c] (s < c in
+        // the order) is set iff fmaf(alpha, d(s,c), -d(v,c)) <= 0.
+        for (int c = warp; c < nr; c += kSmallThreads / 32) {
+            const float dvc = s.sd[c];
+            const int cr = s.srow[c];
+            bool t0 = false, t1 = false;
+            if (lane < c) {
+                const int sr = s.srow[lane];
+                const float dsc = sr < cr ? T[tri(sr, cr, nrows)] : T[tri(cr, sr, nrows)];
+                t0 = fmaf(a.alpha, dsc, -dvc) <= 0.f;
+            }
+            if (lane + 32 < c) {
+                const int sr = s.srow[lane + 32];
+                const float dsc = sr < cr ? T[tri(sr, cr, nrows)] : T[tri(cr, sr, nrows)];
+                t1 = fmaf(a.alpha, dsc, -dvc) <= 0.f;
+            }
+            const unsigned m0 = __ballot_sync(0xffffffffu, t0);
+            const unsigned m1 = __ballot_sync(0xffffffffu, t1);
+            if (lane == 0) {
+                s.occ[2 * c] = m0;
+                s.occ[2 * c + 1] = m1;
+            }
+        }
+        __syncthreads();
+
         if (warp == 0) {
-            float d[2];
-            int32_t id[2], rr[2];
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int e = lane + 32 * h;
-                const bool valid = e < nr && s.pid[e] >= 0;
-                d[h] = valid ? T[tri(0, 1 + e, nrows)] : INFINITY;
-                id[h] = valid ? s.pid[e] : INT32_MAX;
-                rr[h] = 1 + e;
-            }
-            warp_sort64(d, id, rr);
-            // unique candidates in order: element e keeps if valid and its id
-            // differs from element e-1's (duplicates share (d, id), so they sit together)
-            const int32_t prev0 = __shfl_up_sync(0xffffffffu, id[0], 1);
-            const int32_t last0 = __shfl_sync(0xffffffffu, id[0], 31);
-            const int32_t prev1 = __shfl_up_sync(0xffffffffu, id[1], 1);
-            const bool k0 = id[0] != INT32_MAX && !(lane > 0 && prev0 == id[0]);
-            const bool k1 = id[1] != INT32_MAX && !(lane > 0 ? prev1 == id[1] : last0 == id[1]);
-            const unsigned m0 = __ballot_sync(0xffffffffu, k0);
-            const unsigned m1 = __ballot_sync(0xffffffffu, k1);
-            const int c0 = __popc(m0);
-            const int np = c0 + __popc(m1);
-            if (k0) {
-                const int p = __popc(m0 & lanemask_lt());
-                s.sd[p] = d[0]; s.sid[p] = id[0]; s.srow[p] = rr[0];
-            }
-            if (k1) {
-                const int p = c0 + __popc(m1 & lanemask_lt());
-                s.sd[p] = d[1]; s.sid[p] = id[1]; s.srow[p] = rr[1];
-            }
-            __syncwarp();
+            // live positions: valid and not a repeat of the previous id
+            const bool a0 = lane < nr && s.sid[lane] != INT32_MAX &&
+                            (lane == 0 || s.sid[lane - 1] != s.sid[lane]);
+            const bool a1 = lane + 32 < nr && s.sid[lane + 32] != INT32_MAX &&
+                            s.sid[lane + 31] != s.sid[lane + 32];
+            const unsigned long long live = (unsigned long long)__ballot_sync(0xffffffffu, a0) |
+                                            ((unsigned long long)__ballot_sync(0xffffffffu, a1) << 32);
+            const int np = __popcll(live);
+            unsigned long long kept = 0;
             int nk = 0;
             if (a.keep_all_if_fit && np <= R) {
-                for (int j = lane; j < np; j += 32) s.kid[j] = s.sid[j];
+                kept = live;
                 nk = np;
             } else {
-                for (int c = 0; c < np && nk < R; ++c) {
-                    const float dvc = s.sd[c];
-                    const int cr = s.srow[c];
-                    bool occ = false;
-                    for (int j0 = 0; j0 < nk && !occ; j0 += 32) {
-                        const int j = j0 + lane;
-                        bool t = false;
-                        if (j < nk) {
-                            const int kr = s.krow[j];
-                            const float dsc = kr < cr ? T[tri(kr, cr, nrows)] : T[tri(cr, kr, nrows)];
-                            t = fmaf(a.alpha, dsc, -dvc) <= 0.f;
-                        }
-                        occ = __any_sync(0xffffffffu, t);
-                    }
-                    if (!occ) {
-                        if (lane == 0) {
-                            s.krow[nk] = cr;
-                            s.kid[nk] = s.sid[c];
-                        }
+                // the greedy walk (every lane runs it on the same values)
+                for (int c = 0; c < nr && nk < R; ++c) {
+                    if (!((live >> c) & 1ull)) continue;
+                    const unsigned long long oc = (unsigned long long)s.occ[2 * c] |
+                                                  ((unsigned long long)s.occ[2 * c + 1] << 32);
+                    if (!(oc & kept)) {
+                        kept |= 1ull << c;
                         ++nk;
-                        __syncwarp();
                     }
                 }
             }
-            __syncwarp();
             int32_t *out = a.out + (a.out_by_index ? i : (int64_t)owner) * R;
-            for (int j = lane; j < R; j += 32) out[j] = j < nk ? s.kid[j] : -1;
+            const bool k0 = (kept >> lane) & 1ull, k1 = (kept >> (lane + 32)) & 1ull;
+            const int p0 = __popcll(kept & ((1ull << lane) - 1ull));
+            const int p1 = __popcll(kept & ((1ull << (lane + 32)) - 1ull));
+            const int32_t id0 = k0 ? s.sid[lane] : -1, id1 = k1 ? s.sid[lane + 32] : -1;
+            if (k0) out[p0] = id0;
+            if (k1) out[p1] = id1;
+            for (int j = nk + lane; j < R; j += 32) out[j] = -1;
             if (a.eu) {
-                int done = 0;
+                const bool e0 = k0 && id0 >= a.emit_lo && id0 < a.emit_hi;
+                const bool e1 = k1 && id1 >= a.emit_lo && id1 < a.emit_hi;
+                const unsigned b0 = __ballot_sync(0xffffffffu, e0);
+                const unsigned b1 = __ballot_sync(0xffffffffu, e1);
+                const int cnt = __popc(b0) + __popc(b1);
                 int base = 0;
-                int cnt = 0;
-                for (int j0 = 0; j0 < nk; j0 += 32) {
-                    const int j = j0 + lane;
-                    cnt += __popc(__ballot_sync(0xffffffffu, j < nk && s.kid[j] >= a.emit_lo &&
-                                                                 s.kid[j] < a.emit_hi));
-                }
                 if (lane == 0 && cnt) base = (int)atomicAdd(a.ecount, (unsigned long long)cnt);
                 base = __shfl_sync(0xffffffffu, base, 0);
-                for (int j0 = 0; j0 < nk; j0 += 32) {
-                    const int j = j0 + lane;
-                    const bool e = j < nk && s.kid[j] >= a.emit_lo && s.kid[j] < a.emit_hi;
-                    const unsigned m = __ballot_sync(0xffffffffu, e);
-                    if (e) {
-                        const int slot = base + done + __popc(m & lanemask_lt());
-                        a.eu[slot] = s.kid[j];
-                        a.ev[slot] = owner;
-                    }
-                    done += __popc(m);
+                if (e0) {
+                    const int slot = base + __popc(b0 & lanemask_lt());
+                    a.eu[slot] = id0;
+                    a.ev[slot] = owner;
+                }
+                if (e1) {
+                    const int slot = base + __popc(b0) + __popc(b1 & lanemask_lt());
+                    a.eu[slot] = id1;
+                    a.ev[slot] = owner;
                 }
             }
         }

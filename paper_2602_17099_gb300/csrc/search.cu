@@ -27,24 +27,19 @@ constexpr int kSearchWarps = 4;
 constexpr int kProbes = 12;
 constexpr int kCandMax = 64;   // candidates evaluated per batch
 
-// Beam buffer c (0 or 1) holds EFMAX distances then EFMAX ids at
-// beam + c * 2 * EFMAX words; indexing by arithmetic keeps it out of local memory.
+// The candidate set C: EFMAX distances, then EFMAX ids (expanded flag in bit 31).
 struct WarpSmem {
-    float *beam;
-    int efmax;
+    float *bd;
+    int32_t *bi;
     int32_t *hash;
     float *cd;
     int32_t *ci;
     float *sd;
     int32_t *si;
-    __device__ __forceinline__ float *bd(int c) const { return beam + c * 2 * efmax; }
-    __device__ __forceinline__ int32_t *bi(int c) const {
-        return reinterpret_cast<int32_t *>(beam + c * 2 * efmax + efmax);
-    }
 };
 
 __host__ __device__ constexpr size_t warp_smem_bytes(int efmax, int hbits) {
-    return (size_t)efmax * 16 + ((size_t)4 << hbits) + kCandMax * 8 + 32 * 8;
+    return (size_t)efmax * 8 + ((size_t)4 << hbits) + kCandMax * 16;
 }
 
 template <int F4>
@@ -73,11 +68,10 @@ __device__ __forceinline__ bool hash_insert(int32_t *hash, int hbits, int32_t id
 
 // Evaluates up to 64 candidate ids (two per lane: c0 = list[lane],
 // c1 = list[32 + lane]) and merges the new ones into C.
-template <int F4>
+template <int F4, int EFMAX>
 __device__ __forceinline__ void process(const SearchArgs &a, WarpSmem &w, int hbits,
                                         const float4 (&q)[Layout<F4>::V], int32_t c0, int32_t c1,
-                                        int &cur, int &size, bool &overflow,
-                                        unsigned long long &ndc) {
+                                        int &size, bool &overflow, unsigned long long &ndc) {
     using Lay = Layout<F4>;
     constexpr int G = Lay::G, V = Lay::V, RPI = Lay::RPI, U = Lay::U;
     const int lane = threadIdx.x & 31;
@@ -133,53 +127,74 @@ __device__ __forceinline__ void process(const SearchArgs &a, WarpSmem &w, int hb
     }
     __syncwarp();
 
-    // Merge, 32 candidates at a time.
+    // Survivors: candidates that beat the worst entry of a full C (and, after
+    // a hash overflow, are not in C already), compacted into (sd, si).
+    int m = 0;
     for (int b0 = 0; b0 < c; b0 += 32) {
         const int j = b0 + lane;
         float d = INFINITY;
         int32_t id = INT32_MAX;
-        bool valid = j < c;
-        if (valid) {
+        bool keep = j < c;
+        if (keep) {
             d = w.cd[j];
             id = w.ci[j];
         }
-        if (valid && size == ef)
-            valid = lex_less(d, id, w.bd(cur)[ef - 1], w.bi(cur)[ef - 1] & kIdMask);
-        if (valid && overflow) {
+        if (keep && size == ef) keep = lex_less(d, id, w.bd[ef - 1], w.bi[ef - 1] & kIdMask);
+        if (keep && overflow) {
             for (int i = 0; i < size; ++i)
-                if ((w.bi(cur)[i] & kIdMask) == id) { valid = false; break; }
+                if ((w.bi[i] & kIdMask) == id) { keep = false; break; }
+            for (int i = 0; keep && i < b0 + lane; ++i)   // a lossy hash can repeat an id
+                if (w.ci[i] == id) keep = false;
         }
-        if (!valid) { d = INFINITY; id = INT32_MAX; }
-        // +inf distances never enter C: keep the sentinel strictly last
-        warp_sort32(d, id);
-        const int32_t pid = __shfl_up_sync(0xffffffffu, id, 1);
-        const bool keep = id != INT32_MAX && !(lane > 0 && pid == id);
         const unsigned km = __ballot_sync(0xffffffffu, keep);
-        const int mm = __popc(km);
         if (keep) {
-            const int rk = __popc(km & lanemask_lt());
+            const int rk = m + __popc(km & lanemask_lt());
             w.sd[rk] = d;
             w.si[rk] = id;
         }
-        __syncwarp();
-        if (mm == 0) continue;
-        const int nxt = cur ^ 1;
-        for (int i = lane; i < size; i += 32) {
-            const float od = w.bd(cur)[i];
-            const int32_t oi = w.bi(cur)[i];
-            const int pos = i + lower_bound_lex(w.sd, w.si, mm, od, oi & kIdMask);
-            if (pos < ef) { w.bd(nxt)[pos] = od; w.bi(nxt)[pos] = oi; }
-        }
-        if (lane < mm) {
-            const float nd = w.sd[lane];
-            const int32_t ni = w.si[lane];
-            const int pos = lane + lower_bound_lex(w.bd(cur), w.bi(cur), size, nd, ni);
-            if (pos < ef) { w.bd(nxt)[pos] = nd; w.bi(nxt)[pos] = ni; }
-        }
-        __syncwarp();
-        cur = nxt;
-        size = min(ef, size + mm);
+        m += __popc(km);
     }
+    __syncwarp();
+    if (m == 0) return;
+    // Merge by ranks, in place: old entry i moves to i + #{new < it}; new entry
+    // k goes to #{new < it} + #{old < it}; entries past ef fall off.
+    constexpr int PER = EFMAX / 32;
+    float od[PER];
+    int32_t oi[PER];
+    int sh[PER];
+#pragma unroll
+    for (int t = 0; t < PER; ++t) {
+        const int i = lane + 32 * t;
+        od[t] = i < size ? w.bd[i] : INFINITY;
+        oi[t] = i < size ? w.bi[i] : INT32_MAX;
+        sh[t] = 0;
+    }
+    const float nd0 = lane < m ? w.sd[lane] : INFINITY;
+    const int32_t ni0 = lane < m ? w.si[lane] : INT32_MAX;
+    const float nd1 = lane + 32 < m ? w.sd[lane + 32] : INFINITY;
+    const int32_t ni1 = lane + 32 < m ? w.si[lane + 32] : INT32_MAX;
+    int r0 = 0, r1 = 0;
+    for (int k = 0; k < m; ++k) {
+        const float dk = w.sd[k];
+        const int32_t ik = w.si[k];
+        r0 += lex_less(dk, ik, nd0, ni0);
+        r1 += lex_less(dk, ik, nd1, ni1);
+#pragma unroll
+        for (int t = 0; t < PER; ++t) sh[t] += lex_less(dk, ik, od[t], oi[t] & kIdMask);
+    }
+    if (lane < m) r0 += lower_bound_lex(w.bd, w.bi, size, nd0, ni0);
+    if (lane + 32 < m) r1 += lower_bound_lex(w.bd, w.bi, size, nd1, ni1);
+    __syncwarp();
+#pragma unroll
+    for (int t = 0; t < PER; ++t) {
+        const int i = lane + 32 * t;
+        const int pos = i + sh[t];
+        if (i < size && pos < ef) { w.bd[pos] = od[t]; w.bi[pos] = oi[t]; }
+    }
+    if (lane < m && r0 < ef) { w.bd[r0] = nd0; w.bi[r0] = ni0; }
+    if (lane + 32 < m && r1 < ef) { w.bd[r1] = nd1; w.bi[r1] = ni1; }
+    __syncwarp();
+    size = min(ef, size + m);
 }
 
 template <int F4, int EFMAX>
@@ -192,13 +207,13 @@ search_kernel(const SearchArgs a, int hbits) {
     const int warp = threadIdx.x >> 5;
     unsigned char *base = smem + (size_t)warp * warp_smem_bytes(EFMAX, hbits);
     WarpSmem w;
-    w.beam = reinterpret_cast<float *>(base);
-    w.efmax = EFMAX;
-    w.hash = reinterpret_cast<int32_t *>(w.beam + 4 * EFMAX);
+    w.bd = reinterpret_cast<float *>(base);
+    w.bi = reinterpret_cast<int32_t *>(w.bd + EFMAX);
+    w.hash = w.bi + EFMAX;
     w.cd = reinterpret_cast<float *>(w.hash + (1 << hbits));
     w.ci = reinterpret_cast<int32_t *>(w.cd + kCandMax);
     w.sd = reinterpret_cast<float *>(w.ci + kCandMax);
-    w.si = reinterpret_cast<int32_t *>(w.sd + 32);
+    w.si = reinterpret_cast<int32_t *>(w.sd + kCandMax);
     const int H = 1 << hbits;
     const int sub = lane % G;
 
@@ -220,7 +235,7 @@ search_kernel(const SearchArgs a, int hbits) {
         for (int i = lane; i < H; i += 32) w.hash[i] = -1;
         __syncwarp();
 
-        int cur = 0, size = 0;
+        int size = 0;
         bool overflow = false;
         unsigned long long ndc = 0, nexp = 0;
 
@@ -233,11 +248,11 @@ search_kernel(const SearchArgs a, int hbits) {
                 int32_t c1 = s0 + 32 + lane < a.n_seeds ? srow[s0 + 32 + lane] : -1;
                 if (c0 >= a.n_base) c0 = -1;
                 if (c1 >= a.n_base) c1 = -1;
-                process<F4>(a, w, hbits, q, c0, c1, cur, size, overflow, ndc);
+                process<F4, EFMAX>(a, w, hbits, q, c0, c1, size, overflow, ndc);
             }
         } else {
             const int32_t e = a.seed_mode == kSeedSelf ? qrow : a.seed_const;
-            process<F4>(a, w, hbits, q, lane == 0 ? e : -1, -1, cur, size, overflow, ndc);
+            process<F4, EFMAX>(a, w, hbits, q, lane == 0 ? e : -1, -1, size, overflow, ndc);
         }
 
         // Expansion loop: nearest unexpanded entry first.
@@ -245,21 +260,21 @@ search_kernel(const SearchArgs a, int hbits) {
             int found = -1;
             for (int b = 0; b < size; b += 32) {
                 const int i = b + lane;
-                const bool un = i < size && w.bi(cur)[i] >= 0;
+                const bool un = i < size && w.bi[i] >= 0;
                 const unsigned m = __ballot_sync(0xffffffffu, un);
                 if (m) { found = b + __ffs(m) - 1; break; }
             }
             if (found < 0) break;
-            const int32_t u = w.bi(cur)[found];
+            const int32_t u = w.bi[found];
             __syncwarp();
-            if (lane == 0) w.bi(cur)[found] = u | kExpandedBit;
+            if (lane == 0) w.bi[found] = u | kExpandedBit;
             __syncwarp();
             ++nexp;
             const int32_t *nb = a.adj + (int64_t)u * a.r_in;
             for (int j0 = 0; j0 < a.r_in; j0 += 64) {
                 const int32_t c0 = j0 + lane < a.r_in ? nb[j0 + lane] : -1;
                 const int32_t c1 = j0 + 32 + lane < a.r_in ? nb[j0 + 32 + lane] : -1;
-                process<F4>(a, w, hbits, q, c0, c1, cur, size, overflow, ndc);
+                process<F4, EFMAX>(a, w, hbits, q, c0, c1, size, overflow, ndc);
             }
         }
 
@@ -271,13 +286,13 @@ search_kernel(const SearchArgs a, int hbits) {
         int written = 0;
         for (int b = 0; b < size && written < a.k; b += 32) {
             const int i = b + lane;
-            const int32_t id = i < size ? (w.bi(cur)[i] & kIdMask) : -1;
+            const int32_t id = i < size ? (w.bi[i] & kIdMask) : -1;
             const bool keep = i < size && id != self;
             const unsigned m = __ballot_sync(0xffffffffu, keep);
             const int pos = written + __popc(m & lanemask_lt());
             if (keep && pos < a.k) {
                 oid[pos] = id + a.id_offset;
-                if (od) od[pos] = w.bd(cur)[i];
+                if (od) od[pos] = w.bd[i];
             }
             written += __popc(m);
         }
