@@ -101,8 +101,35 @@ struct Ctl {
     int32_t *work;           // several work counters
     unsigned long long *stats;  // per search slot s: [2s] ndc, [2s+1] expansions
     unsigned long long *ecount;
+    unsigned long long *rechecks;  // prune decisions re-decided in FP32
     int32_t *scratch_i;      // misc int
 };
+
+// Quantized copies of the rows for the tensor-core prune (prec 1 or 2).
+struct QuantBufs {
+    int32_t prec = 0;
+    void *q = nullptr;
+    float *scale = nullptr, *err = nullptr, *norm = nullptr;
+};
+
+void take_quant(Bump &b, int64_t n, int32_t dim, int32_t prec, QuantBufs &qb) {
+    qb.prec = prec;
+    if (prec == 0) return;
+    qb.q = b.take<char>((size_t)n * dim * (prec == 2 ? 1 : 2));
+    qb.scale = b.take<float>(n);
+    qb.err = b.take<float>(n);
+    qb.norm = b.take<float>(n);
+}
+
+void apply_quant(PruneArgs &a, const QuantBufs *qb, unsigned long long *rechecks) {
+    a.rechecks = rechecks;
+    if (!qb || qb->prec == 0) return;
+    a.prec = qb->prec;
+    a.qrows = qb->q;
+    a.qscale = qb->scale;
+    a.qerr = qb->err;
+    a.qnorm = qb->norm;
+}
 
 constexpr int kWorkSlots = 16;
 
@@ -113,12 +140,14 @@ void take_ctl(Bump &b, Ctl &c, int64_t max_owners = 0) {
     c.work = b.take<int32_t>(kWorkSlots);
     c.stats = b.take<unsigned long long>(8);
     c.ecount = b.take<unsigned long long>(1);
+    c.rechecks = b.take<unsigned long long>(1);
     c.scratch_i = b.take<int32_t>(4);
 }
 
 rnsm_status ctl_reset(const Ctl &c, cudaStream_t st) {
     CK(cudaMemsetAsync(c.err, 0, sizeof(int32_t), st));
     CK(cudaMemsetAsync(c.stats, 0, 8 * sizeof(unsigned long long), st));
+    CK(cudaMemsetAsync(c.rechecks, 0, sizeof(unsigned long long), st));
     return RNSM_OK;
 }
 
@@ -130,6 +159,7 @@ rnsm_status check_err_word(const Ctl &c, cudaStream_t st) {
     if (err & 2) return fail(RNSM_EGRAPH, "vectors hold a non-finite value");
     if (err & 16) return fail(RNSM_EGRAPH, "a prune pool exceeded 4096 candidates");
     if (err & 32) return fail(RNSM_EGRAPH, "a reverse-kNN row exceeded 4096 entries");
+    if (err & 64) return fail(RNSM_ETIMEOUT, "a tensor-core prune tile did not complete in time");
     if (err) return fail(RNSM_ECUDA, "device error word 0x%x", err);
     return RNSM_OK;
 }
@@ -246,7 +276,8 @@ void take_rev(Bump &b, int64_t nkeys, int64_t cap, RevBufs &r) {
 rnsm_status reverse_into(const SegTable &tab, int32_t dim, const rnsm_params &p, int32_t *lists,
                          const int32_t *eu, const int32_t *ev, int64_t cap,
                          const unsigned long long *count, int32_t key_lo, int64_t nkeys,
-                         int32_t csr_max_bound, const RevBufs &r, const Ctl &c, cudaStream_t st) {
+                         int32_t csr_max_bound, const RevBufs &r, const Ctl &c, cudaStream_t st,
+                         const QuantBufs *qb = nullptr) {
     CK(launch_bucket(eu, ev, cap, count, nkeys, key_lo, r.offs, r.cursor, r.ids, r.scan_tmp,
                      r.scan_bytes, st));
     int32_t csr_max = csr_max_bound;
@@ -272,6 +303,7 @@ rnsm_status reverse_into(const SegTable &tab, int32_t dim, const rnsm_params &p,
     a.csr_max = csr_max;
     a.out = lists;
     a.err = c.err;
+    apply_quant(a, qb, c.rechecks);
     return run_prune(a, c.work + 6, c, st);
 }
 
@@ -498,13 +530,17 @@ rnsm_status rnsm_prune(const float *vecs, int64_t n, int32_t dim, const int32_t 
     if (R < 1 || R > 64) return fail(RNSM_EINVAL, "R outside [1, 64]");
     if (!(std::isfinite(alpha) && alpha >= 0.f)) return fail(RNSM_EINVAL, "bad alpha");
     if (metric != 0 && metric != 1) return fail(RNSM_EINVAL, "unknown metric");
-    if (prec != RNSM_PREC_FP32) return fail(RNSM_EINVAL, "only the FP32 prune is available here");
+    if (prec < RNSM_PREC_FP32 || prec > RNSM_PREC_FP8) return fail(RNSM_EINVAL, "unknown precision");
+    const int32_t qprec = prune_tc_supported(dim, prec) ? prec : 0;  // else the FP32 kernels
     if (nv == 0) return RNSM_OK;
     Bump b;
     Ctl c;
+    QuantBufs qb;
     take_ctl(b, c, nv);
+    take_quant(b, n, dim, qprec, qb);
     TRY(ws_acquire(b.off, b));
     take_ctl(b, c, nv);
+    take_quant(b, n, dim, qprec, qb);
     TRY(ctl_reset(c, st));
     TRY(validate_on_device(vecs, n, dim, nullptr, 0, c, st));
     CK(launch_validate_ids(owners, nv, n, 0, c.err, st));
@@ -531,6 +567,8 @@ rnsm_status rnsm_prune(const float *vecs, int64_t n, int32_t dim, const int32_t 
     a.out = out;
     a.out_by_index = 1;
     a.err = c.err;
+    if (qprec) CK(launch_quantize(tab, n, dim, qprec, qb.q, qb.scale, qb.err, qb.norm, st));
+    apply_quant(a, &qb, c.rechecks);
     TRY(run_prune(a, c.work + 8, c, st));
     TRY(check_err_word(c, st));
     return RNSM_OK;
@@ -711,10 +749,11 @@ struct MergeBufs {
     int32_t *pivots, *followers, *pivot_of, *res, *eu, *ev;
     void *piv_tmp;
     RevBufs rev;
+    QuantBufs qb;
 };
 
-void carve_merge(Bump &b, const rnsm_params &p, int64_t ns_max, int64_t nt_max, Ctl &c,
-                 MergeBufs &m) {
+void carve_merge(Bump &b, const rnsm_params &p, int64_t ns_max, int64_t nt_max, int64_t n_all,
+                 int32_t dim, int32_t qprec, Ctl &c, MergeBufs &m) {
     take_ctl(b, c, ns_max > nt_max ? ns_max : nt_max);
     m.nplus = b.take<int32_t>(ns_max * p.k_plus);
     m.rk_keys = b.take<int32_t>(ns_max * p.k_rev);
@@ -732,6 +771,7 @@ void carve_merge(Bump &b, const rnsm_params &p, int64_t ns_max, int64_t nt_max, 
     m.eu = b.take<int32_t>(ns_max * p.R);
     m.ev = b.take<int32_t>(ns_max * p.R);
     take_rev(b, nt_max, ns_max * p.R, m.rev);
+    take_quant(b, n_all, dim, qprec, m.qb);
 }
 
 // CUDA events at the step boundaries of one plan edge (S1 .. S7).
@@ -770,12 +810,16 @@ struct SrcCache {
 size_t rnsm_workspace_size(const rnsm_segment *segs, int32_t m, const rnsm_params *pin) {
     rnsm_params p;
     if (resolve_params(pin, p) != RNSM_OK || !segs || m < 1) return 0;
-    int64_t nmax = 0;
-    for (int32_t s = 0; s < m; ++s) nmax = segs[s].n > nmax ? segs[s].n : nmax;
+    int64_t nmax = 0, nall = 0;
+    for (int32_t s = 0; s < m; ++s) {
+        nmax = segs[s].n > nmax ? segs[s].n : nmax;
+        nall += segs[s].n;
+    }
+    const int32_t qprec = prune_tc_supported(segs[0].dim, p.prec) ? p.prec : 0;
     Bump b;
     Ctl c;
     MergeBufs mb;
-    carve_merge(b, p, nmax, nmax, c, mb);
+    carve_merge(b, p, nmax, nmax, nall, segs[0].dim, qprec, c, mb);
     return b.off;
 }
 
@@ -822,12 +866,13 @@ rnsm_status rnsm_merge(const rnsm_segment *segs, int32_t m, const rnsm_params *p
         nmax = segs[s].n > nmax ? segs[s].n : nmax;
     }
     tab.off[m] = off;
+    const int32_t qprec = prune_tc_supported(dim, p.prec) ? p.prec : 0;  // else FP32 kernels
     Bump b;
     Ctl c;
     MergeBufs mb;
-    carve_merge(b, p, nmax, nmax, c, mb);
+    carve_merge(b, p, nmax, nmax, off, dim, qprec, c, mb);
     TRY(ws_acquire(b.off, b));
-    carve_merge(b, p, nmax, nmax, c, mb);
+    carve_merge(b, p, nmax, nmax, off, dim, qprec, c, mb);
     TRY(ctl_reset(c, st));
     for (int32_t s = 0; s < m; ++s)
         TRY(validate_on_device(segs[s].vecs, segs[s].n, dim, segs[s].adj, segs[s].r_in, c, st));
@@ -835,6 +880,8 @@ rnsm_status rnsm_merge(const rnsm_segment *segs, int32_t m, const rnsm_params *p
     for (int32_t s = 0; s < m; ++s)
         CK(launch_init_lists(segs[s].adj, segs[s].n, segs[s].r_in, (int32_t)tab.off[s],
                              out_adj + tab.off[s] * p.R, p.R, st));
+    if (qprec)  // BF16 / E4M3 copies of every row for the tensor-core prune tiles
+        CK(launch_quantize(tab, off, dim, qprec, mb.qb.q, mb.qb.scale, mb.qb.err, mb.qb.norm, st));
     clk.mark(1, st);
     CK(cudaStreamSynchronize(st));
     clk.add(phase_ms, 0, 1, 0);
@@ -1030,12 +1077,13 @@ rnsm_status rnsm_merge(const rnsm_segment *segs, int32_t m, const rnsm_params *p
             q.ev = mb.ev;
             q.ecount = c.ecount;
             q.err = c.err;
+            apply_quant(q, &mb.qb, c.rechecks);
             TRY(run_prune(q, c.work + 8, c, st));
         }
         clk.mark(6, st);
         // S7: reverse edges into the target (counting sort by u, then prune).
         TRY(reverse_into(tab, dim, p, out_adj, mb.eu, mb.ev, ns * p.R, c.ecount, t0, nt, -1,
-                         mb.rev, c, st));
+                         mb.rev, c, st, &mb.qb));
         clk.mark(7, st);
         unsigned long long ne = 0;
         CK(cudaMemcpyAsync(&ne, c.ecount, sizeof(ne), cudaMemcpyDeviceToHost, st));
@@ -1056,7 +1104,10 @@ rnsm_status rnsm_merge(const rnsm_segment *segs, int32_t m, const rnsm_params *p
             stats->search_queries[i] = queries[i];
         }
         stats->launches = launches_so_far() - launches0;
-        stats->rechecks = 0;
+        unsigned long long rc = 0;
+        CK(cudaMemcpyAsync(&rc, c.rechecks, sizeof(rc), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        stats->rechecks = (int64_t)rc;
         stats->near_ties = 0;
         stats->pivots = n_piv;
         stats->followers = n_fol;

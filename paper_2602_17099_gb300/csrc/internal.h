@@ -80,6 +80,12 @@ struct PruneArgs {
     int32_t *eu;
     int32_t *ev;
     unsigned long long *ecount;
+    int32_t prec;             // 0 FP32; 1 BF16 / 2 FP8 tiles on the tensor cores
+    const void *qrows;        // quantized rows by global id [N * dim] (BF16 or E4M3)
+    const float *qscale;      // FP8 per-row scale
+    const float *qerr;        // residual norms ||x - x~||
+    const float *qnorm;       // row norms ||x||
+    unsigned long long *rechecks;  // decisions re-decided in FP32
     int32_t *work;
     int32_t *work2;           // second zeroed counter (overflow pass)
     int32_t *ovf_list;        // [n_owners]: owners whose pool exceeds the small-pool kernel
@@ -88,6 +94,14 @@ struct PruneArgs {
 };
 
 cudaError_t launch_prune(const PruneArgs &a, cudaStream_t st);
+
+// Tensor-core small-pool prune (BF16 / FP8 tiles with FP32 re-decisions).
+bool prune_tc_supported(int dim, int prec);
+cudaError_t launch_prune_tc(const PruneArgs &a, cudaStream_t st);
+// Rows of the segment table to BF16 (prec 1) or E4M3 with per-row scale (prec 2),
+// plus residual norms and row norms.
+cudaError_t launch_quantize(const SegTable &segs, int64_t n, int32_t dim, int prec, void *q,
+                            float *scale, float *err, float *norm, cudaStream_t st);
 
 // Counting sort of (key, val) pairs by key into CSR (K3).
 // keys/vals [cap], the number of valid pairs at *count (device) or n_host.

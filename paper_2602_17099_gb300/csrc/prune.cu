@@ -736,6 +736,8 @@ cudaError_t launch_general(const PruneArgs &a, const int32_t *idx_list,
 
 }  // namespace
 
+cudaError_t launch_small(const PruneArgs &a, cudaStream_t st);
+
 cudaError_t launch_prune(const PruneArgs &a, cudaStream_t st) {
     if (a.n_owners <= 0) return cudaSuccess;
     if (a.R > 64 || a.dim > 1024 || (a.dim & 3)) return cudaErrorInvalidValue;
@@ -743,6 +745,23 @@ cudaError_t launch_prune(const PruneArgs &a, cudaStream_t st) {
     if (!small_ok) return launch_general(a, nullptr, nullptr, st);
     cudaError_t e = cudaMemsetAsync(a.ovf_count, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
+    if (a.prec != 0 && a.qrows && prune_tc_supported(a.dim, a.prec)) {
+        e = launch_prune_tc(a, st);
+    } else {
+        e = launch_small(a, st);
+    }
+    if (e != cudaSuccess) return e;
+    if (a.lenA + a.lenB + (a.csr_offs ? a.csr_max : 0) <= kSmallMax) return cudaSuccess;
+    // owners whose pools exceeded 64 raw candidates (the count stays on the device)
+    PruneArgs b = a;
+    b.work = a.work2;
+    e = cudaMemsetAsync(b.work, 0, sizeof(int32_t), st);
+    if (e != cudaSuccess) return e;
+    return launch_general(b, a.ovf_list, a.ovf_count, st);
+}
+
+cudaError_t launch_small(const PruneArgs &a, cudaStream_t st) {
+    cudaError_t e;
     cudaFuncSetAttribute(prune_small_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
@@ -756,15 +775,7 @@ cudaError_t launch_prune(const PruneArgs &a, cudaStream_t st) {
     if (want < grid) grid = want;
     prune_small_kernel<<<(unsigned)grid, kSmallThreads, 0, st>>>(a, chunk);
     note_launches(1);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    if (a.lenA + a.lenB + (a.csr_offs ? a.csr_max : 0) <= kSmallMax) return cudaSuccess;
-    // owners whose pools exceeded 64 raw candidates (the count stays on the device)
-    PruneArgs b = a;
-    b.work = a.work2;
-    e = cudaMemsetAsync(b.work, 0, sizeof(int32_t), st);
-    if (e != cudaSuccess) return e;
-    return launch_general(b, a.ovf_list, a.ovf_count, st);
+    return cudaGetLastError();
 }
 
 }  // namespace rnsm

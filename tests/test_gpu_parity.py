@@ -330,3 +330,43 @@ def test_merge_host_and_device_pivots_agree(rn):
     b, sb = rn.merge(tsegs, rn.params(16, 32, 1.2, flags=rn.FLAG_HOST_PIVOTS))
     np.testing.assert_array_equal(host(a), host(b))
     assert sa["pivots"] == sb["pivots"]
+
+
+# ------------------------------------------- precision pattern (BF16 / FP8)
+
+@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("kind,d,w", [("gauss", 32, 64), ("gauss", 128, 48), ("deep", 96, 64),
+                                      ("sift", 128, 64), ("embed", 256, 40), ("gauss", 128, 100)])
+def test_low_precision_prune_equals_fp32(rn, prec, kind, d, w):
+    n = 3000
+    X = {"gauss": lambda: gen.gaussian(n, d, 90),
+         "deep": lambda: gen.deep_like(n, 91, d=d),
+         "sift": lambda: gen.sift_like(n, 92, d=d),
+         "embed": lambda: gen.embed_like(n, 93, d=d, n_comp=50)}[kind]()
+    metric = oracle.IP if kind in ("deep", "embed") else oracle.L2
+    owners, pool = _pools(n, w, 7 * d + w, 800)
+    Xd, od, pd_ = dev(X), dev(owners), dev(pool)
+    want = rn.prune(Xd, od, pd_, 32, 1.2, metric=metric)
+    got = rn.prune(Xd, od, pd_, 32, 1.2, metric=metric, prec=prec)
+    np.testing.assert_array_equal(host(got), host(want))
+    want2 = rn.prune(Xd, od, pd_, 32, 1.2, metric=metric, keep_all_if_fit=True)
+    got2 = rn.prune(Xd, od, pd_, 32, 1.2, metric=metric, keep_all_if_fit=True, prec=prec)
+    np.testing.assert_array_equal(host(got2), host(want2))
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_low_precision_merge_equals_fp32(rn, prec):
+    for segs, metric in ((gen.tiny_case(n_per_seg=3000)[0], oracle.L2),
+                         ([gen.sift_like(4000, 95, d=128), gen.sift_like(3000, 96, d=128)],
+                          oracle.L2),
+                         ([gen.deep_like(3000, 97, d=96), gen.deep_like(2500, 98, d=96)],
+                          oracle.IP)):
+        R, L = (16, 32) if segs[0].shape[1] == 32 else (32, 64)
+        gs = [oracle.build_graph(s, R, L, 1.2, metric=metric) for s in segs]
+        tsegs = [(dev(s), dev(g), e) for s, (g, e) in zip(segs, gs)]
+        a, sa = rn.merge(tsegs, rn.params(R, L, 1.2, metric=metric))
+        b, sb = rn.merge(tsegs, rn.params(R, L, 1.2, metric=metric, prec=prec))
+        np.testing.assert_array_equal(host(b), host(a))
+        assert sa["rechecks"] == 0
+        if segs[0].dtype == np.float32 and not (segs[0] == np.rint(segs[0])).all():
+            assert sb["rechecks"] > 0       # real-valued data: some decisions re-decided
