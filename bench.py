@@ -60,6 +60,11 @@ def barrier(dist):
         dist.barrier()
 
 
+def whole_job_rate(units_per_rank_step: int, steps: int, world: int, ms_max: float) -> float:
+    """Units all ranks processed divided by the slowest rank's time (1/s)."""
+    return units_per_rank_step * steps * world / (ms_max / 1000.0)
+
+
 def allmax(dist, x: float) -> float:
     if dist is None:
         return x
@@ -263,7 +268,7 @@ def run_ours(args, ws, rank, local):
     clocks = sampler.stop()
     ms = ev0.elapsed_time(ev1)
     ms_max = allmax(dist, ms)
-    value = N * args.steps * ws / (ms_max / 1000.0)
+    value = whole_job_rate(N, args.steps, ws, ms_max)
 
     # roofline of the search kernel (S1, S4, S5 launches), from the
     # library's CUDA events on the launching stream and its NDC counters
@@ -296,6 +301,34 @@ def run_ours(args, ws, rank, local):
     phase_ms = {nm: sum(st["phase_ms"][i] for st in stats) / len(stats)
                 for i, nm in enumerate(phases)}
 
+    # precision pattern: the same merge with BF16 / FP8 prune tiles (tensor
+    # cores + FP32 re-decisions); their graphs must equal the FP32 graph
+    modes = {}
+    ref_out = out.clone()
+    for name, prec in (("bf16", rn.BF16), ("fp8", rn.FP8)):
+        pq = rn.params(R, L, ALPHA, prec=prec)
+        oq = torch.empty_like(out)
+        for _ in range(2):
+            rn.merge(tsegs, pq, out=oq)
+        torch.cuda.synchronize()
+        q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        qs = []
+        nq = max(3, args.steps // 2)
+        q0.record(stream)
+        for _ in range(nq):
+            _, st = rn.merge(tsegs, pq, out=oq)
+            qs.append(st)
+        q1.record(stream)
+        torch.cuda.synchronize()
+        qms = q0.elapsed_time(q1) / nq
+        modes[name] = {"ms_per_step": qms, "value": N / (qms / 1000.0), "unit": UNIT,
+                       "identical_to_fp32": bool(torch.equal(oq, ref_out)),
+                       "rechecks_per_step": qs[-1]["rechecks"],
+                       "prune_ms": round(sum(st["phase_ms"][6] + st["phase_ms"][7]
+                                             for st in qs) / nq, 3)}
+    modes["fp32"] = {"ms_per_step": ms_max / args.steps,
+                     "prune_ms": round(phase_ms["S6_source_prune"] + phase_ms["S7_reverse_edges"], 3)}
+
     # end to end through the public API with host buffers
     pin_v = [s_.cpu().pin_memory() for s_ in vd]
     pin_g = [g.cpu().pin_memory() for g, _ in graphs]
@@ -318,7 +351,7 @@ def run_ours(args, ws, rank, local):
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = allmax(dist, e0.elapsed_time(e1))
-    e2e = {"value": N * args.steps * ws / (e2e_ms / 1000.0), "unit": UNIT,
+    e2e = {"value": whole_job_rate(N, args.steps, ws, e2e_ms), "unit": UNIT,
            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
     rec = None
@@ -349,6 +382,7 @@ def run_ours(args, ws, rank, local):
                            "pivots": stats[-1]["pivots"], "followers": stats[-1]["followers"],
                            "ndc_per_step": stats[-1]["ndc"]},
                 "clocks": clocks, "e2e": e2e, "gpu_launches": int(launches),
+                "precision_modes": modes,
                 "roofline": roofline, "cpu_baseline": base}
         print(json.dumps(line), flush=True)
     barrier(dist)

@@ -1,0 +1,56 @@
+"""The benchmark's multi-rank path (independent replicas, one per GPU):
+barrier, max-over-ranks timing and whole-job aggregation, exercised with two
+gloo ranks on the CPU."""
+import os
+import socket
+import sys
+
+import pytest
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, q):
+    sys.path.insert(0, ROOT)
+    os.environ.update({"RANK": str(rank), "WORLD_SIZE": str(world), "LOCAL_RANK": str(rank),
+                       "MASTER_ADDR": "127.0.0.1", "MASTER_PORT": str(port)})
+    import bench
+    ws, r, _ = bench.dist_env()
+    dist = bench.init_dist(ws)
+    bench.barrier(dist)
+    slowest = bench.allmax(dist, 10.0 * (r + 1))      # rank 1 is the slow one
+    rate = bench.whole_job_rate(1000, 4, ws, slowest)
+    bench.barrier(dist)
+    dist.destroy_process_group()
+    q.put((r, slowest, rate))
+
+
+def test_two_gloo_ranks_take_the_slowest_rank_and_sum_units():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    got = sorted(q.get(timeout=5) for _ in range(2))
+    for r, slowest, rate in got:
+        assert slowest == 20.0                      # max over ranks
+        assert rate == pytest.approx(1000 * 4 * 2 / 0.020)
+
+
+def test_single_rank_needs_no_process_group():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.init_dist(1) is None
+    assert bench.allmax(None, 3.5) == 3.5
+    assert bench.whole_job_rate(10, 2, 1, 1000.0) == 20.0
