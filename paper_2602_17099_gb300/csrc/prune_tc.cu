@@ -48,9 +48,13 @@ __device__ float exact_dist(const float *a, const float *b, int dim, int metric)
     return metric == 0 ? acc : 1.0f - acc;
 }
 
+constexpr int kPairs = kRows * (kRows - 1) / 2;
+
 struct TcSmem {
     float Gd[kRows];          // scaled Gram diagonal
-    float e[kRows];           // residual norms
+    float e[kRows];           // residual norms of the stored quantisation
+    float ep[kRows];          // residual norms of the per-tile re-quantisation (L2)
+    float sc[kRows];          // per-row scale of the staged tile row
     float nr[kRows];          // row norms
     int32_t pid[kMax];
     const float *rptr[kRows];
@@ -64,6 +68,9 @@ struct TcSmem {
     int32_t sid[kMax];
     int32_t srow[kMax];
     uint32_t occ[2 * kMax];
+    uint32_t undecided[kPairs];   // (s << 16) | c of occlusion tests the tile cannot settle
+    int32_t need_ex[kMax];
+    int n_undecided;
     uint64_t bar;
     uint32_t tmem_slot;
 };
@@ -147,12 +154,73 @@ __global__ void __launch_bounds__(kThreads) prune_tc_kernel(const PruneArgs a, i
             s.nr[r] = a.qnorm[g];
             s.rptr[r] = seg_row(a.segs, g, dim);
         }
-        // 2. stage the quantized rows
-        for (int e = tid; e < nrows * chunks; e += kThreads) {
-            const int r = e / chunks, j = e - r * chunks;
-            const int32_t g = r == 0 ? owner : (s.pid[r - 1] >= 0 ? s.pid[r - 1] : owner);
-            const uint4 v = *reinterpret_cast<const uint4 *>(Q + (int64_t)g * row_bytes + 16 * j);
-            *reinterpret_cast<uint4 *>(tile + (r >> 3) * SBO + j * LBO + (r & 7) * 16) = v;
+        // 2. stage the tile rows.  L2: every row is re-centred on the owner
+        //    (x~_r - x~_v, re-quantised), so the Gram entries are of the size of
+        //    the distances themselves and the tile is free of cancellation;
+        //    integer-valued data stays exact.  IP: the stored rows as they are.
+        if (metric == 0) {
+            for (int r = tid; r < nrows; r += kThreads) {
+                const int32_t g = r == 0 ? owner : (s.pid[r - 1] >= 0 ? s.pid[r - 1] : owner);
+                float res = 0.f, dsum = 0.f, scale = 1.f;
+                if (kFp8) {
+                    const __nv_fp8_e4m3 *xr = reinterpret_cast<const __nv_fp8_e4m3 *>(Q) + (int64_t)g * dim;
+                    const __nv_fp8_e4m3 *xo = reinterpret_cast<const __nv_fp8_e4m3 *>(Q) + (int64_t)owner * dim;
+                    const float sg = a.qscale[g], so = a.qscale[owner];
+                    float mx = 0.f;
+                    for (int k = 0; k < dim; ++k)
+                        mx = fmaxf(mx, fabsf(sg * static_cast<float>(xr[k]) - so * static_cast<float>(xo[k])));
+                    scale = mx > 0.f ? mx / 448.0f : 1.0f;
+                    for (int j = 0; j < chunks; ++j) {
+                        uint32_t w[4];
+                        unsigned char *wb = reinterpret_cast<unsigned char *>(w);
+                        for (int k = 0; k < 16; ++k) {
+                            const int kk = 16 * j + k;
+                            const float dlt = sg * static_cast<float>(xr[kk]) - so * static_cast<float>(xo[kk]);
+                            const __nv_fp8_e4m3 q(dlt / scale);
+                            const float rr = dlt - scale * static_cast<float>(q);
+                            res = fmaf(rr, rr, res);
+                            dsum = fmaf(dlt, dlt, dsum);
+                            wb[k] = *reinterpret_cast<const unsigned char *>(&q);
+                        }
+                        *reinterpret_cast<uint4 *>(tile + (r >> 3) * SBO + j * LBO + (r & 7) * 16) =
+                            make_uint4(w[0], w[1], w[2], w[3]);
+                    }
+                } else {
+                    const uint4 *xr = reinterpret_cast<const uint4 *>(Q + (int64_t)g * row_bytes);
+                    const uint4 *xo = reinterpret_cast<const uint4 *>(Q + (int64_t)owner * row_bytes);
+                    for (int j = 0; j < chunks; ++j) {
+                        const uint4 av = xr[j], ov = xo[j];
+                        const __nv_bfloat16 *ab = reinterpret_cast<const __nv_bfloat16 *>(&av);
+                        const __nv_bfloat16 *ob = reinterpret_cast<const __nv_bfloat16 *>(&ov);
+                        __nv_bfloat16 q[8];
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) {
+                            const float dlt = __bfloat162float(ab[k]) - __bfloat162float(ob[k]);
+                            q[k] = __float2bfloat16_rn(dlt);
+                            const float rr = dlt - __bfloat162float(q[k]);
+                            res = fmaf(rr, rr, res);
+                            dsum = fmaf(dlt, dlt, dsum);
+                        }
+                        *reinterpret_cast<uint4 *>(tile + (r >> 3) * SBO + j * LBO + (r & 7) * 16) =
+                            *reinterpret_cast<const uint4 *>(q);
+                    }
+                }
+                // re-quantisation residual, plus the rounding of the FP32 subtraction
+                s.ep[r] = (res > 0.f ? sqrtf(res) * 1.001f : 0.f) + 2.4e-7f * sqrtf(dsum);
+                s.sc[r] = scale;
+            }
+        } else {
+            for (int e = tid; e < nrows * chunks; e += kThreads) {
+                const int r = e / chunks, j = e - r * chunks;
+                const int32_t g = r == 0 ? owner : (s.pid[r - 1] >= 0 ? s.pid[r - 1] : owner);
+                const uint4 v = *reinterpret_cast<const uint4 *>(Q + (int64_t)g * row_bytes + 16 * j);
+                *reinterpret_cast<uint4 *>(tile + (r >> 3) * SBO + j * LBO + (r & 7) * 16) = v;
+            }
+            for (int r = tid; r < nrows; r += kThreads) {
+                const int32_t g = r == 0 ? owner : (s.pid[r - 1] >= 0 ? s.pid[r - 1] : owner);
+                s.ep[r] = 0.f;
+                s.sc[r] = kFp8 ? a.qscale[g] : 1.f;
+            }
         }
         tc::fence_async_shared();
         tc::fence_before_sync();
@@ -180,8 +248,7 @@ __global__ void __launch_bounds__(kThreads) prune_tc_kernel(const PruneArgs a, i
         tc::fence_after_sync();
         // 4. epilogue: diagonal first, then the triangle with its bounds
         const int row = 32 * warp + lane;
-        const float srow_scale = (kFp8 && row < nrows)
-            ? a.qscale[row == 0 ? owner : (s.pid[row - 1] >= 0 ? s.pid[row - 1] : owner)] : 1.f;
+        const float srow_scale = row < nrows ? s.sc[row] : 1.f;
         if (warp < 3) {
             for (int c = 0; c < kN / 16; ++c) {
                 uint32_t r[16];
@@ -202,10 +269,9 @@ __global__ void __launch_bounds__(kThreads) prune_tc_kernel(const PruneArgs a, i
                     for (int q = 0; q < 16; ++q) {
                         const int col = 16 * c + q;
                         if (col <= row || col >= nrows) continue;
-                        const float cs = kFp8 ? a.qscale[s.pid[col - 1] >= 0 ? s.pid[col - 1] : owner] : 1.f;
-                        const float g = __uint_as_float(r[q]) * srow_scale * cs;
+                        const float g = __uint_as_float(r[q]) * srow_scale * s.sc[col];
                         const float gi = s.Gd[row], gj = s.Gd[col];
-                        const float E = s.e[row] + s.e[col];
+                        const float E = s.e[row] + s.e[col] + s.ep[row] + s.ep[col];
                         float dt, bq, bc, bf;
                         if (metric == 0) {
                             dt = gi + gj - 2.0f * g;
@@ -268,32 +334,34 @@ __global__ void __launch_bounds__(kThreads) prune_tc_kernel(const PruneArgs a, i
             s.srow[r] = 1 + j;
         }
         __syncthreads();
-        // 7. occluder masks; an undecided test is recomputed in FP32
+        // 7. occluder masks.  Pass 1 settles what the tile can and lists the
+        //    rest; pass 2 computes the missing exact owner distances; pass 3
+        //    recomputes every listed test in FP32, one test per thread.
+        if (tid == 0) s.n_undecided = 0;
+        for (int c = tid; c < kMax; c += kThreads) s.need_ex[c] = 0;
+        __syncthreads();
         for (int c = warp; c < nr; c += kThreads / 32) {
             const int cr = s.srow[c];
-            const bool cex = s.sid[c] != INT32_MAX && s.ex[cr - 1];
+            const bool cvalid = s.sid[c] != INT32_MAX;
+            const bool cex = cvalid && s.ex[cr - 1];
             const float dvc = s.sd[c];
-            const float bvc = cex ? 0.f : s.Bt[tri(0, cr, nrows)];
+            const float bvc = cex ? 0.f : (cvalid ? s.Bt[tri(0, cr, nrows)] : 0.f);
             bool t[2] = {false, false};
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int sp = lane + 32 * h;
-                if (sp >= c || s.sid[sp] == INT32_MAX || s.sid[c] == INT32_MAX) continue;
+                if (sp >= c || s.sid[sp] == INT32_MAX || !cvalid) continue;
                 const int sr = s.srow[sp];
                 const int tt = sr < cr ? tri(sr, cr, nrows) : tri(cr, sr, nrows);
                 const float dsc = s.T[tt], bsc = s.Bt[tt];
                 const float lo = a.alpha * (dsc - bsc) - (dvc + bvc);
                 const float hi = a.alpha * (dsc + bsc) - (dvc - bvc);
                 const float slack = 1e-6f * (a.alpha * (fabsf(dsc) + bsc) + fabsf(dvc) + bvc);
-                if (lo - slack > 0.f) {
-                    t[h] = false;
-                } else if (hi + slack < 0.f) {
+                if (hi + slack < 0.f) {
                     t[h] = true;
-                } else {
-                    const float xs = exact_dist(s.rptr[sr], s.rptr[cr], dim, metric);
-                    const float xv = cex ? dvc : exact_dist(s.rptr[0], s.rptr[cr], dim, metric);
-                    t[h] = fmaf(a.alpha, xs, -xv) <= 0.f;
-                    ++rechecks;
+                } else if (!(lo - slack > 0.f)) {
+                    s.undecided[atomicAdd(&s.n_undecided, 1)] = ((uint32_t)sp << 16) | (uint32_t)c;
+                    if (!cex) s.need_ex[cr - 1] = 1;
                 }
             }
             const unsigned m0 = __ballot_sync(0xffffffffu, t[0]);
@@ -302,6 +370,25 @@ __global__ void __launch_bounds__(kThreads) prune_tc_kernel(const PruneArgs a, i
                 s.occ[2 * c] = m0;
                 s.occ[2 * c + 1] = m1;
             }
+        }
+        __syncthreads();
+        for (int j = tid; j < nr; j += kThreads) {
+            if (s.need_ex[j] && !s.ex[j]) {
+                s.dx[j] = exact_dist(s.rptr[0], s.rptr[1 + j], dim, metric);
+                s.ex[j] = 1;
+                ++rechecks;
+            }
+        }
+        __syncthreads();
+        const int nu = s.n_undecided;
+        for (int u = tid; u < nu; u += kThreads) {
+            const uint32_t code = s.undecided[u];
+            const int sp = (int)(code >> 16), c = (int)(code & 0xffffu);
+            const int sr = s.srow[sp], cr = s.srow[c];
+            const float xs = exact_dist(s.rptr[sr], s.rptr[cr], dim, metric);
+            const float xv = s.ex[cr - 1] ? s.dx[cr - 1] : s.sd[c];
+            if (fmaf(a.alpha, xs, -xv) <= 0.f) atomicOr(&s.occ[2 * c + (sp >> 5)], 1u << (sp & 31));
+            ++rechecks;
         }
         __syncthreads();
         // 8. greedy walk and output (as the FP32 small-pool prune)
