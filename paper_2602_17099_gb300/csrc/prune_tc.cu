@@ -38,10 +38,23 @@ constexpr long kSpinLimit = 1L << 26;
 
 __device__ __forceinline__ int tri(int a, int b, int n) { return a * (2 * n - a - 1) / 2 + (b - a - 1); }
 
-// The FP32 prune's distance: one fmaf chain over the dimensions in order.
+// The FP32 prune's distance: one fmaf chain over the dimensions in order
+// (loads issued eight float4 ahead; the arithmetic order is unchanged).
 __device__ float exact_dist(const float *a, const float *b, int dim, int metric) {
     float acc = 0.f;
-    for (int f = 0; f < (dim >> 2); ++f) {
+    const int F4 = dim >> 2;
+    int f = 0;
+    for (; f + 8 <= F4; f += 8) {
+        float4 x[8], y[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            x[u] = ldg4(a + 4 * (f + u));
+            y[u] = ldg4(b + 4 * (f + u));
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc = metric == 0 ? l2_acc(acc, x[u], y[u]) : ip_acc(acc, x[u], y[u]);
+    }
+    for (; f < F4; ++f) {
         const float4 x = ldg4(a + 4 * f), y = ldg4(b + 4 * f);
         acc = metric == 0 ? l2_acc(acc, x, y) : ip_acc(acc, x, y);
     }
@@ -70,6 +83,9 @@ struct TcSmem {
     uint32_t occ[2 * kMax];
     uint32_t undecided[kPairs];   // (s << 16) | c of occlusion tests the tile cannot settle
     int32_t need_ex[kMax];
+    float res[kRows];          // staging reductions (L2)
+    float dsum[kRows];
+    uint32_t mx[kRows];
     int n_undecided;
     uint64_t bar;
     uint32_t tmem_slot;
@@ -160,54 +176,76 @@ __global__ void __launch_bounds__(kThreads) prune_tc_kernel(const PruneArgs a, i
         //    integer-valued data stays exact.  IP: the stored rows as they are.
         if (metric == 0) {
             for (int r = tid; r < nrows; r += kThreads) {
-                const int32_t g = r == 0 ? owner : (s.pid[r - 1] >= 0 ? s.pid[r - 1] : owner);
-                float res = 0.f, dsum = 0.f, scale = 1.f;
-                if (kFp8) {
-                    const __nv_fp8_e4m3 *xr = reinterpret_cast<const __nv_fp8_e4m3 *>(Q) + (int64_t)g * dim;
-                    const __nv_fp8_e4m3 *xo = reinterpret_cast<const __nv_fp8_e4m3 *>(Q) + (int64_t)owner * dim;
+                s.res[r] = 0.f;
+                s.dsum[r] = 0.f;
+                s.mx[r] = 0u;
+            }
+            __syncthreads();
+            if (kFp8) {  // per-row scale of the centred row: max |x~_r - x~_v| / 448
+                for (int e = tid; e < nrows * chunks; e += kThreads) {
+                    const int r = e / chunks, j = e - r * chunks;
+                    const int32_t g = r == 0 ? owner : (s.pid[r - 1] >= 0 ? s.pid[r - 1] : owner);
+                    const uint4 av = *reinterpret_cast<const uint4 *>(Q + (int64_t)g * row_bytes + 16 * j);
+                    const uint4 ov = *reinterpret_cast<const uint4 *>(Q + (int64_t)owner * row_bytes + 16 * j);
+                    const __nv_fp8_e4m3 *ab = reinterpret_cast<const __nv_fp8_e4m3 *>(&av);
+                    const __nv_fp8_e4m3 *ob = reinterpret_cast<const __nv_fp8_e4m3 *>(&ov);
                     const float sg = a.qscale[g], so = a.qscale[owner];
-                    float mx = 0.f;
-                    for (int k = 0; k < dim; ++k)
-                        mx = fmaxf(mx, fabsf(sg * static_cast<float>(xr[k]) - so * static_cast<float>(xo[k])));
-                    scale = mx > 0.f ? mx / 448.0f : 1.0f;
-                    for (int j = 0; j < chunks; ++j) {
-                        uint32_t w[4];
-                        unsigned char *wb = reinterpret_cast<unsigned char *>(w);
-                        for (int k = 0; k < 16; ++k) {
-                            const int kk = 16 * j + k;
-                            const float dlt = sg * static_cast<float>(xr[kk]) - so * static_cast<float>(xo[kk]);
-                            const __nv_fp8_e4m3 q(dlt / scale);
-                            const float rr = dlt - scale * static_cast<float>(q);
-                            res = fmaf(rr, rr, res);
-                            dsum = fmaf(dlt, dlt, dsum);
-                            wb[k] = *reinterpret_cast<const unsigned char *>(&q);
-                        }
-                        *reinterpret_cast<uint4 *>(tile + (r >> 3) * SBO + j * LBO + (r & 7) * 16) =
-                            make_uint4(w[0], w[1], w[2], w[3]);
+                    float m = 0.f;
+#pragma unroll
+                    for (int k = 0; k < 16; ++k)
+                        m = fmaxf(m, fabsf(sg * static_cast<float>(ab[k]) - so * static_cast<float>(ob[k])));
+                    atomicMax(&s.mx[r], __float_as_uint(m));
+                }
+                __syncthreads();
+            }
+            for (int e = tid; e < nrows * chunks; e += kThreads) {
+                const int r = e / chunks, j = e - r * chunks;
+                const int32_t g = r == 0 ? owner : (s.pid[r - 1] >= 0 ? s.pid[r - 1] : owner);
+                const uint4 av = *reinterpret_cast<const uint4 *>(Q + (int64_t)g * row_bytes + 16 * j);
+                const uint4 ov = *reinterpret_cast<const uint4 *>(Q + (int64_t)owner * row_bytes + 16 * j);
+                float res = 0.f, dsum = 0.f;
+                uint4 outv;
+                if (kFp8) {
+                    const __nv_fp8_e4m3 *ab = reinterpret_cast<const __nv_fp8_e4m3 *>(&av);
+                    const __nv_fp8_e4m3 *ob = reinterpret_cast<const __nv_fp8_e4m3 *>(&ov);
+                    const float sg = a.qscale[g], so = a.qscale[owner];
+                    const float mxr = __uint_as_float(s.mx[r]);
+                    const float scale = mxr > 0.f ? mxr / 448.0f : 1.0f;
+                    unsigned char *ob8 = reinterpret_cast<unsigned char *>(&outv);
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) {
+                        const float dlt = sg * static_cast<float>(ab[k]) - so * static_cast<float>(ob[k]);
+                        const __nv_fp8_e4m3 q(dlt / scale);
+                        const float rr = dlt - scale * static_cast<float>(q);
+                        res = fmaf(rr, rr, res);
+                        dsum = fmaf(dlt, dlt, dsum);
+                        ob8[k] = *reinterpret_cast<const unsigned char *>(&q);
                     }
                 } else {
-                    const uint4 *xr = reinterpret_cast<const uint4 *>(Q + (int64_t)g * row_bytes);
-                    const uint4 *xo = reinterpret_cast<const uint4 *>(Q + (int64_t)owner * row_bytes);
-                    for (int j = 0; j < chunks; ++j) {
-                        const uint4 av = xr[j], ov = xo[j];
-                        const __nv_bfloat16 *ab = reinterpret_cast<const __nv_bfloat16 *>(&av);
-                        const __nv_bfloat16 *ob = reinterpret_cast<const __nv_bfloat16 *>(&ov);
-                        __nv_bfloat16 q[8];
+                    const __nv_bfloat16 *ab = reinterpret_cast<const __nv_bfloat16 *>(&av);
+                    const __nv_bfloat16 *ob = reinterpret_cast<const __nv_bfloat16 *>(&ov);
+                    __nv_bfloat16 *qo = reinterpret_cast<__nv_bfloat16 *>(&outv);
 #pragma unroll
-                        for (int k = 0; k < 8; ++k) {
-                            const float dlt = __bfloat162float(ab[k]) - __bfloat162float(ob[k]);
-                            q[k] = __float2bfloat16_rn(dlt);
-                            const float rr = dlt - __bfloat162float(q[k]);
-                            res = fmaf(rr, rr, res);
-                            dsum = fmaf(dlt, dlt, dsum);
-                        }
-                        *reinterpret_cast<uint4 *>(tile + (r >> 3) * SBO + j * LBO + (r & 7) * 16) =
-                            *reinterpret_cast<const uint4 *>(q);
+                    for (int k = 0; k < 8; ++k) {
+                        const float dlt = __bfloat162float(ab[k]) - __bfloat162float(ob[k]);
+                        qo[k] = __float2bfloat16_rn(dlt);
+                        const float rr = dlt - __bfloat162float(qo[k]);
+                        res = fmaf(rr, rr, res);
+                        dsum = fmaf(dlt, dlt, dsum);
                     }
                 }
-                // re-quantisation residual, plus the rounding of the FP32 subtraction
-                s.ep[r] = (res > 0.f ? sqrtf(res) * 1.001f : 0.f) + 2.4e-7f * sqrtf(dsum);
-                s.sc[r] = scale;
+                *reinterpret_cast<uint4 *>(tile + (r >> 3) * SBO + j * LBO + (r & 7) * 16) = outv;
+                if (res > 0.f) atomicAdd(&s.res[r], res);
+                if (dsum > 0.f) atomicAdd(&s.dsum[r], dsum);
+            }
+            __syncthreads();
+            for (int r = tid; r < nrows; r += kThreads) {
+                // re-quantisation residual (rounded up: the atomic sum's order varies),
+                // plus the rounding of the FP32 subtraction
+                const float res = s.res[r];
+                s.ep[r] = (res > 0.f ? sqrtf(res) * 1.001f : 0.f) + 2.4e-7f * sqrtf(s.dsum[r]);
+                const float mxr = __uint_as_float(s.mx[r]);
+                s.sc[r] = kFp8 ? (mxr > 0.f ? mxr / 448.0f : 1.0f) : 1.0f;
             }
         } else {
             for (int e = tid; e < nrows * chunks; e += kThreads) {
