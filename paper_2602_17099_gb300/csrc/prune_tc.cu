@@ -71,8 +71,6 @@ struct TcSmem {
     float nr[kRows];          // row norms
     int32_t pid[kMax];
     const float *rptr[kRows];
-    float T[kRows * (kRows - 1) / 2];   // d~ triangle
-    float Bt[kRows * (kRows - 1) / 2];  // bound triangle
     float dx[kMax];            // exact owner distance (valid if ex[c])
     int32_t ex[kMax];
     float kd[kMax];
@@ -81,7 +79,6 @@ struct TcSmem {
     int32_t sid[kMax];
     int32_t srow[kMax];
     uint32_t occ[2 * kMax];
-    uint32_t undecided[kPairs];   // (s << 16) | c of occlusion tests the tile cannot settle
     int32_t need_ex[kMax];
     float res[kRows];          // staging reductions (L2)
     float dsum[kRows];
@@ -124,6 +121,12 @@ __global__ void __launch_bounds__(kThreads) prune_tc_kernel(const PruneArgs a, i
     tc::fence_after_sync();
     const uint32_t taddr = s.tmem_slot;
     const uint32_t tbase = tc::smem_u32(tile);
+    // Once an owner's MMA has completed its staged rows are dead: the tile
+    // buffer then holds the d~ triangle, the bound triangle and the list of
+    // undecided tests ((s << 16) | c).
+    float *const T = reinterpret_cast<float *>(tile);
+    float *const Bt = T + kPairs;
+    uint32_t *const undecided = reinterpret_cast<uint32_t *>(Bt + kPairs);
     uint32_t phase = 0;
     unsigned long long rechecks = 0;
 
@@ -324,8 +327,8 @@ __global__ void __launch_bounds__(kThreads) prune_tc_kernel(const PruneArgs a, i
                             bf = gam * s.nr[row] * s.nr[col] + 1.2e-7f;
                         }
                         const int t = tri(row, col, nrows);
-                        s.T[t] = dt;
-                        s.Bt[t] = 1.01f * (bq + bc + bf) + 1e-30f;
+                        T[t] = dt;
+                        Bt[t] = 1.01f * (bq + bc + bf) + 1e-30f;
                     }
                 }
             }
@@ -336,11 +339,11 @@ __global__ void __launch_bounds__(kThreads) prune_tc_kernel(const PruneArgs a, i
         for (int c = tid; c < kMax; c += kThreads) {
             s.ex[c] = 0;
             if (c < nr && s.pid[c] >= 0) {
-                const float dc = s.T[tri(0, 1 + c, nrows)], bc = s.Bt[tri(0, 1 + c, nrows)];
+                const float dc = T[tri(0, 1 + c, nrows)], bc = Bt[tri(0, 1 + c, nrows)];
                 bool clash = false;
                 for (int k = 0; k < nr && !clash; ++k) {
                     if (k == c || s.pid[k] < 0) continue;
-                    const float dk = s.T[tri(0, 1 + k, nrows)], bk = s.Bt[tri(0, 1 + k, nrows)];
+                    const float dk = T[tri(0, 1 + k, nrows)], bk = Bt[tri(0, 1 + k, nrows)];
                     clash = fabsf(dc - dk) <= (bc + bk) * 1.0001f;
                 }
                 if (clash) {
@@ -354,7 +357,7 @@ __global__ void __launch_bounds__(kThreads) prune_tc_kernel(const PruneArgs a, i
         // 6. order by (distance, id): exact keys where resolved, else the tile's
         for (int j = tid; j < kMax; j += kThreads) {
             const bool valid = j < nr && s.pid[j] >= 0;
-            s.kd[j] = valid ? (s.ex[j] ? s.dx[j] : s.T[tri(0, 1 + j, nrows)]) : INFINITY;
+            s.kd[j] = valid ? (s.ex[j] ? s.dx[j] : T[tri(0, 1 + j, nrows)]) : INFINITY;
             s.kix[j] = valid ? s.pid[j] : INT32_MAX;
         }
         __syncthreads();
@@ -383,7 +386,7 @@ __global__ void __launch_bounds__(kThreads) prune_tc_kernel(const PruneArgs a, i
             const bool cvalid = s.sid[c] != INT32_MAX;
             const bool cex = cvalid && s.ex[cr - 1];
             const float dvc = s.sd[c];
-            const float bvc = cex ? 0.f : (cvalid ? s.Bt[tri(0, cr, nrows)] : 0.f);
+            const float bvc = cex ? 0.f : (cvalid ? Bt[tri(0, cr, nrows)] : 0.f);
             bool t[2] = {false, false};
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
@@ -391,14 +394,14 @@ __global__ void __launch_bounds__(kThreads) prune_tc_kernel(const PruneArgs a, i
                 if (sp >= c || s.sid[sp] == INT32_MAX || !cvalid) continue;
                 const int sr = s.srow[sp];
                 const int tt = sr < cr ? tri(sr, cr, nrows) : tri(cr, sr, nrows);
-                const float dsc = s.T[tt], bsc = s.Bt[tt];
+                const float dsc = T[tt], bsc = Bt[tt];
                 const float lo = a.alpha * (dsc - bsc) - (dvc + bvc);
                 const float hi = a.alpha * (dsc + bsc) - (dvc - bvc);
                 const float slack = 1e-6f * (a.alpha * (fabsf(dsc) + bsc) + fabsf(dvc) + bvc);
                 if (hi + slack < 0.f) {
                     t[h] = true;
                 } else if (!(lo - slack > 0.f)) {
-                    s.undecided[atomicAdd(&s.n_undecided, 1)] = ((uint32_t)sp << 16) | (uint32_t)c;
+                    undecided[atomicAdd(&s.n_undecided, 1)] = ((uint32_t)sp << 16) | (uint32_t)c;
                     if (!cex) s.need_ex[cr - 1] = 1;
                 }
             }
@@ -420,7 +423,7 @@ __global__ void __launch_bounds__(kThreads) prune_tc_kernel(const PruneArgs a, i
         __syncthreads();
         const int nu = s.n_undecided;
         for (int u = tid; u < nu; u += kThreads) {
-            const uint32_t code = s.undecided[u];
+            const uint32_t code = undecided[u];
             const int sp = (int)(code >> 16), c = (int)(code & 0xffffu);
             const int sr = s.srow[sp], cr = s.srow[c];
             const float xs = exact_dist(s.rptr[sr], s.rptr[cr], dim, metric);
@@ -558,23 +561,33 @@ bool prune_tc_supported(int dim, int prec) {
 
 cudaError_t launch_prune_tc(const PruneArgs &a, cudaStream_t st) {
     const bool fp8 = a.prec == 2;
-    const size_t tile = (size_t)kM * a.dim * (fp8 ? 1 : 2);
+    size_t dyn = (size_t)kM * a.dim * (fp8 ? 1 : 2);
+    const size_t after = (size_t)kPairs * 12;   // triangles + undecided list
+    if (dyn < after) dyn = after;
     auto kern = fp8 ? prune_tc_kernel<true> : prune_tc_kernel<false>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     if (e != cudaSuccess) return e;
     cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    int dev = 0, sms = 0, per_sm = 0;
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, kern);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, smem_sm = 0, regs_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, tile);
-    if (e != cudaSuccess) return e;
-    // every resident CTA holds kTmemCols of the SM's 512 tensor-memory columns
-    per_sm = per_sm < 1 ? 1 : (per_sm > 512 / kTmemCols ? 512 / kTmemCols : per_sm);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+    // resident CTAs per SM: shared memory (plus 1 KB reserved per CTA), registers,
+    // and the SM's 512 tensor-memory columns (kTmemCols per CTA)
+    int per_sm = smem_sm / (int)(fa.sharedSizeBytes + dyn + 1024);
+    const int by_regs = regs_sm / ((fa.numRegs > 0 ? fa.numRegs : 64) * kThreads);
+    if (by_regs < per_sm) per_sm = by_regs;
+    if (per_sm > 512 / kTmemCols) per_sm = 512 / kTmemCols;
+    if (per_sm < 1) per_sm = 1;
     const int chunk = a.skip_empty_csr ? 32 : 1;
     int64_t grid = (int64_t)sms * per_sm;
     const int64_t want = (a.n_owners + chunk - 1) / chunk;
     if (want < grid) grid = want;
-    kern<<<(unsigned)grid, kThreads, tile, st>>>(a, chunk);
+    kern<<<(unsigned)grid, kThreads, dyn, st>>>(a, chunk);
     note_launches(1);
     return cudaGetLastError();
 }
