@@ -15,7 +15,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
-OUT_DIR = os.path.join(HERE, "_build")
+OUT_DIR = os.environ.get("RNSM_BUILD_DIR") or os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "librnsm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
@@ -51,6 +51,7 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
         return LIB
     nvcc = _nvcc()
     inc = ["-I", os.path.join(ROOT, "include"), "-I", CSRC]
+    extra = tuple(extra) + tuple(os.environ.get("RNSM_NVCC_EXTRA", "").split())
 
     def compile_one(src):
         obj = os.path.join(OUT_DIR, os.path.basename(src) + ".o")

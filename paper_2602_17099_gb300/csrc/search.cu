@@ -42,6 +42,13 @@ __host__ __device__ constexpr size_t warp_smem_bytes(int efmax, int hbits) {
     return (size_t)efmax * 8 + ((size_t)4 << hbits) + kCandMax * 16;
 }
 
+#ifndef RNSM_SEARCH_UMUL2
+#define RNSM_SEARCH_UMUL2 2   // rows in flight, in halves of the default
+#endif
+#ifndef RNSM_SEARCH_MINB
+#define RNSM_SEARCH_MINB 1
+#endif
+
 template <int F4>
 struct Layout {
     static constexpr int quarter = F4 / 4 > 0 ? F4 / 4 : 1;
@@ -49,7 +56,8 @@ struct Layout {
                            : quarter >= 4 ? 4 : quarter >= 2 ? 2 : 1;
     static constexpr int V = (F4 + G - 1) / G;   // float4 per lane per row
     static constexpr int RPI = 32 / G;            // rows per step
-    static constexpr int U = V <= 4 ? 8 / V : 2;  // steps in flight
+    static constexpr int U0 = V <= 4 ? 8 / V : 2;
+    static constexpr int U = U0 * RNSM_SEARCH_UMUL2 / 2 > 0 ? U0 * RNSM_SEARCH_UMUL2 / 2 : 1;  // steps in flight
 };
 
 __device__ __forceinline__ bool hash_insert(int32_t *hash, int hbits, int32_t id, bool &overflow) {
@@ -198,7 +206,7 @@ __device__ __forceinline__ void process(const SearchArgs &a, WarpSmem &w, int hb
 }
 
 template <int F4, int EFMAX>
-__global__ void __launch_bounds__(kSearchWarps * 32)
+__global__ void __launch_bounds__(kSearchWarps * 32, RNSM_SEARCH_MINB)
 search_kernel(const SearchArgs a, int hbits) {
     using Lay = Layout<F4>;
     constexpr int G = Lay::G, V = Lay::V;

@@ -15,7 +15,8 @@ import numpy as np
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "librnsm.so")
+LIB_PATH = os.path.join(os.environ.get("RNSM_BUILD_DIR") or os.path.join(_HERE, "_build"),
+                        "librnsm.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EGRAPH = range(6)
 L2, IP = 0, 1
