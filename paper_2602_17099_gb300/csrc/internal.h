@@ -17,8 +17,9 @@ long long launches_so_far();
 
 enum SeedMode : int32_t { kSeedConst = 0, kSeedSelf = 1, kSeedTable = 2 };
 
-// One batched beam-search launch (Algorithm 1).  Query i reads
-// qvecs[qrow * dim] with qrow = qidx ? qidx[i] : i.
+// One batched beam-search launch (Algorithm 1).  Query i of the launch is
+// query g = q0 + i of the batch; it reads qvecs[qrow * dim] with
+// qrow = qidx ? qidx[g] : g.
 struct SearchArgs {
     const float *base;      // searched vector set [n_base * dim]
     int64_t n_base;
@@ -29,6 +30,7 @@ struct SearchArgs {
     const float *qvecs;
     const int32_t *qidx;    // nullable
     int64_t nq;
+    int64_t q0;             // query i of this launch is query q0 + i of the batch
     int32_t seed_mode;      // SeedMode
     int32_t seed_const;     // kSeedConst: the single entry vertex
     const int32_t *seed_tab;  // kSeedTable: rows of seeds
@@ -49,6 +51,8 @@ struct SearchArgs {
 };
 
 cudaError_t launch_search(const SearchArgs &a, cudaStream_t st);
+// Launch-shape variant the search autotuner chose for (dim, ef), -1 if none yet.
+int search_variant_for(int dim, int ef);
 
 // Occlusion prune (UpdateGraph) of a batch of owners over a segment table.
 // Owner i is global id owner_ids ? owner_ids[i] : owner_base + i.  Its pool

@@ -16,6 +16,11 @@
 // than the worst entry of C (and that bound only tightens) while vertices
 // inside C are deduplicated by id before insertion.
 #include <float.h>
+#include <stdlib.h>
+
+#include <map>
+#include <mutex>
+#include <utility>
 
 #include "internal.h"
 
@@ -38,18 +43,20 @@ struct WarpSmem {
     int32_t *si;
 };
 
-__host__ __device__ constexpr size_t warp_smem_bytes(int efmax, int hbits) {
-    return (size_t)efmax * 8 + ((size_t)4 << hbits) + kCandMax * 16;
+__host__ __device__ constexpr size_t warp_smem_bytes(int efmax, int hslots) {
+    return (size_t)efmax * 8 + (size_t)4 * hslots + kCandMax * 16;
 }
 
-#ifndef RNSM_SEARCH_UMUL2
-#define RNSM_SEARCH_UMUL2 2   // rows in flight, in halves of the default
-#endif
-#ifndef RNSM_SEARCH_MINB
-#define RNSM_SEARCH_MINB 1
-#endif
+// Launch-shape variants (identical results): 0 = half the rows in flight and
+// registers capped for 8 CTAs per SM; 1 = the full rows in flight, 5 CTAs.
+template <int VAR>
+struct Variant {
+    static constexpr int kUMul2 = VAR == 0 ? 1 : 2;  // rows in flight, in halves of U0
+    static constexpr int kMinBlocks = VAR == 0 ? 8 : 5;
+};
+constexpr int kVariants = 2;
 
-template <int F4>
+template <int F4, int UMUL2 = 2>
 struct Layout {
     static constexpr int quarter = F4 / 4 > 0 ? F4 / 4 : 1;
     static constexpr int G = quarter >= 32 ? 32 : quarter >= 16 ? 16 : quarter >= 8 ? 8
@@ -57,18 +64,18 @@ struct Layout {
     static constexpr int V = (F4 + G - 1) / G;   // float4 per lane per row
     static constexpr int RPI = 32 / G;            // rows per step
     static constexpr int U0 = V <= 4 ? 8 / V : 2;
-    static constexpr int U = U0 * RNSM_SEARCH_UMUL2 / 2 > 0 ? U0 * RNSM_SEARCH_UMUL2 / 2 : 1;  // steps in flight
+    static constexpr int U = U0 * UMUL2 / 2 > 0 ? U0 * UMUL2 / 2 : 1;  // steps in flight
 };
 
-__device__ __forceinline__ bool hash_insert(int32_t *hash, int hbits, int32_t id, bool &overflow) {
-    const uint32_t hmask = (1u << hbits) - 1u;
-    uint32_t h = ((uint32_t)id * 0x9E3779B1u) >> (32 - hbits);
+// Open addressing over H slots (any H): multiply-shift start, linear probing.
+__device__ __forceinline__ bool hash_insert(int32_t *hash, int H, int32_t id, bool &overflow) {
+    uint32_t slot = (uint32_t)(((uint64_t)((uint32_t)id * 0x9E3779B1u) * (uint32_t)H) >> 32);
 #pragma unroll 1
     for (int p = 0; p < kProbes; ++p) {
-        uint32_t slot = (h + p) & hmask;
         int32_t old = atomicCAS(&hash[slot], -1, id);
         if (old == -1) return true;
         if (old == id) return false;
+        slot = slot + 1 == (uint32_t)H ? 0u : slot + 1;
     }
     overflow = true;  // treated as unseen; results stay exact (see header)
     return true;
@@ -76,19 +83,19 @@ __device__ __forceinline__ bool hash_insert(int32_t *hash, int hbits, int32_t id
 
 // Evaluates up to 64 candidate ids (two per lane: c0 = list[lane],
 // c1 = list[32 + lane]) and merges the new ones into C.
-template <int F4, int EFMAX>
-__device__ __forceinline__ void process(const SearchArgs &a, WarpSmem &w, int hbits,
+template <int F4, int EFMAX, int VAR>
+__device__ __forceinline__ void process(const SearchArgs &a, WarpSmem &w, int hslots,
                                         const float4 (&q)[Layout<F4>::V], int32_t c0, int32_t c1,
                                         int &size, bool &overflow, unsigned long long &ndc) {
-    using Lay = Layout<F4>;
+    using Lay = Layout<F4, Variant<VAR>::kUMul2>;
     constexpr int G = Lay::G, V = Lay::V, RPI = Lay::RPI, U = Lay::U;
     const int lane = threadIdx.x & 31;
     const int grp = lane / G, sub = lane % G;
     const int ef = a.ef;
 
     bool ovf = false;
-    bool n0 = c0 >= 0 && hash_insert(w.hash, hbits, c0, ovf);
-    bool n1 = c1 >= 0 && hash_insert(w.hash, hbits, c1, ovf);
+    bool n0 = c0 >= 0 && hash_insert(w.hash, hslots, c0, ovf);
+    bool n1 = c1 >= 0 && hash_insert(w.hash, hslots, c1, ovf);
     if (__any_sync(0xffffffffu, ovf)) overflow = true;
     unsigned m0 = __ballot_sync(0xffffffffu, n0);
     unsigned m1 = __ballot_sync(0xffffffffu, n1);
@@ -205,24 +212,24 @@ __device__ __forceinline__ void process(const SearchArgs &a, WarpSmem &w, int hb
     size = min(ef, size + m);
 }
 
-template <int F4, int EFMAX>
-__global__ void __launch_bounds__(kSearchWarps * 32, RNSM_SEARCH_MINB)
-search_kernel(const SearchArgs a, int hbits) {
+template <int F4, int EFMAX, int VAR>
+__global__ void __launch_bounds__(kSearchWarps * 32, Variant<VAR>::kMinBlocks)
+search_kernel(const SearchArgs a, int hslots) {
     using Lay = Layout<F4>;
     constexpr int G = Lay::G, V = Lay::V;
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    unsigned char *base = smem + (size_t)warp * warp_smem_bytes(EFMAX, hbits);
+    unsigned char *base = smem + (size_t)warp * warp_smem_bytes(EFMAX, hslots);
     WarpSmem w;
     w.bd = reinterpret_cast<float *>(base);
     w.bi = reinterpret_cast<int32_t *>(w.bd + EFMAX);
     w.hash = w.bi + EFMAX;
-    w.cd = reinterpret_cast<float *>(w.hash + (1 << hbits));
+    w.cd = reinterpret_cast<float *>(w.hash + hslots);
     w.ci = reinterpret_cast<int32_t *>(w.cd + kCandMax);
     w.sd = reinterpret_cast<float *>(w.ci + kCandMax);
     w.si = reinterpret_cast<int32_t *>(w.sd + kCandMax);
-    const int H = 1 << hbits;
+    const int H = hslots;
     const int sub = lane % G;
 
     unsigned long long ndc_total = 0, nexp_total = 0;
@@ -231,7 +238,8 @@ search_kernel(const SearchArgs a, int hbits) {
         if (lane == 0) qi = atomicAdd(a.work, 1);
         qi = __shfl_sync(0xffffffffu, qi, 0);
         if (qi >= a.nq) break;
-        const int32_t qrow = a.qidx ? a.qidx[qi] : qi;
+        const int64_t gi = a.q0 + qi;  // index in the whole batch
+        const int32_t qrow = a.qidx ? a.qidx[gi] : (int32_t)gi;
 
         float4 q[V];
         const float *qv = a.qvecs + (int64_t)qrow * (4 * F4);
@@ -249,18 +257,18 @@ search_kernel(const SearchArgs a, int hbits) {
 
         // Entry points.
         if (a.seed_mode == kSeedTable) {
-            const int64_t row = a.seed_row ? a.seed_row[qrow] : qi;
+            const int64_t row = a.seed_row ? a.seed_row[qrow] : gi;
             const int32_t *srow = a.seed_tab + row * a.seed_stride;
             for (int s0 = 0; s0 < a.n_seeds; s0 += 64) {
                 int32_t c0 = s0 + lane < a.n_seeds ? srow[s0 + lane] : -1;
                 int32_t c1 = s0 + 32 + lane < a.n_seeds ? srow[s0 + 32 + lane] : -1;
                 if (c0 >= a.n_base) c0 = -1;
                 if (c1 >= a.n_base) c1 = -1;
-                process<F4, EFMAX>(a, w, hbits, q, c0, c1, size, overflow, ndc);
+                process<F4, EFMAX, VAR>(a, w, hslots, q, c0, c1, size, overflow, ndc);
             }
         } else {
             const int32_t e = a.seed_mode == kSeedSelf ? qrow : a.seed_const;
-            process<F4, EFMAX>(a, w, hbits, q, lane == 0 ? e : -1, -1, size, overflow, ndc);
+            process<F4, EFMAX, VAR>(a, w, hslots, q, lane == 0 ? e : -1, -1, size, overflow, ndc);
         }
 
         // Expansion loop: nearest unexpanded entry first.
@@ -282,13 +290,13 @@ search_kernel(const SearchArgs a, int hbits) {
             for (int j0 = 0; j0 < a.r_in; j0 += 64) {
                 const int32_t c0 = j0 + lane < a.r_in ? nb[j0 + lane] : -1;
                 const int32_t c1 = j0 + 32 + lane < a.r_in ? nb[j0 + 32 + lane] : -1;
-                process<F4, EFMAX>(a, w, hbits, q, c0, c1, size, overflow, ndc);
+                process<F4, EFMAX, VAR>(a, w, hslots, q, c0, c1, size, overflow, ndc);
             }
         }
 
         // Output: first k entries of C (optionally without the query vertex).
         const int32_t self = a.exclude_self ? qrow : -1;
-        const int64_t orow = a.out_by_qidx ? qrow : qi;
+        const int64_t orow = a.out_by_qidx ? qrow : gi;
         int32_t *oid = a.out_ids + orow * a.out_stride;
         float *od = a.out_d ? a.out_d + orow * a.out_stride : nullptr;
         int written = 0;
@@ -308,7 +316,7 @@ search_kernel(const SearchArgs a, int hbits) {
             oid[j] = -1;
             if (od) od[j] = FLT_MAX;
         }
-        if (lane == 0 && a.out_ndc) a.out_ndc[qi] = (int64_t)ndc;
+        if (lane == 0 && a.out_ndc) a.out_ndc[gi] = (int64_t)ndc;
         ndc_total += ndc;
         nexp_total += nexp;
         __syncwarp();
@@ -319,61 +327,150 @@ search_kernel(const SearchArgs a, int hbits) {
     }
 }
 
-int hbits_for(int ef) {
-    // NDC runs at ~15-20 per beam entry on degree-32 graphs: 32 slots per
-    // entry keep the load factor near 0.5 (at least 1024, at most 8192 slots)
-    int h = 10;
-    while ((1 << h) < 32 * ef && h < 13) ++h;
-    return h;
+int hslots_for(int ef) {
+    // NDC runs at ~13-20 per beam entry on degree-32 graphs: 24 slots per
+    // entry keep the load factor near 0.6 (at least 1024, a multiple of 32)
+    int h = 24 * ef;
+    if (h < 1024) h = 1024;
+    return (h + 31) & ~31;
 }
 
-template <int F4, int EFMAX>
+template <int F4, int EFMAX, int VAR>
 cudaError_t launch_t(const SearchArgs &a, cudaStream_t st) {
-    const int hbits = hbits_for(a.ef);
-    const size_t smem = (size_t)kSearchWarps * warp_smem_bytes(EFMAX, hbits);
-    auto kern = search_kernel<F4, EFMAX>;
+    const int hslots = hslots_for(a.ef);
+    const size_t smem = (size_t)kSearchWarps * warp_smem_bytes(EFMAX, hslots);
+    auto kern = search_kernel<F4, EFMAX, VAR>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     // the visited hashes live in shared memory: ask for the largest carveout
     cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    int dev = 0, sms = 0, per_sm = 0;
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, kern);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, smem_sm = 0, regs_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kSearchWarps * 32, smem);
-    if (e != cudaSuccess) return e;
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+    int per_sm = smem_sm / (int)(fa.sharedSizeBytes + smem + 1024);
+    const int by_regs = regs_sm / ((fa.numRegs > 0 ? fa.numRegs : 64) * kSearchWarps * 32);
+    if (by_regs < per_sm) per_sm = by_regs;
+    if (per_sm > 2048 / (kSearchWarps * 32)) per_sm = 2048 / (kSearchWarps * 32);
     if (per_sm < 1) per_sm = 1;
     int64_t want = (a.nq + kSearchWarps - 1) / kSearchWarps;
     int64_t grid = (int64_t)sms * per_sm;
     if (want < grid) grid = want < 1 ? 1 : want;
-    kern<<<(unsigned)grid, kSearchWarps * 32, smem, st>>>(a, hbits);
+    kern<<<(unsigned)grid, kSearchWarps * 32, smem, st>>>(a, hslots);
     note_launches(1);
     return cudaGetLastError();
 }
 
-template <int F4>
-cudaError_t launch_ef(const SearchArgs &a, cudaStream_t st) {
-    if (a.ef <= 32) return launch_t<F4, 32>(a, st);
-    if (a.ef <= 64) return launch_t<F4, 64>(a, st);
-    if (a.ef <= 128) return launch_t<F4, 128>(a, st);
-    return launch_t<F4, 256>(a, st);
+template <int F4, int EFMAX>
+cudaError_t launch_var(const SearchArgs &a, int var, cudaStream_t st) {
+    return var == 0 ? launch_t<F4, EFMAX, 0>(a, st) : launch_t<F4, EFMAX, 1>(a, st);
 }
+
+template <int F4>
+cudaError_t launch_ef(const SearchArgs &a, int var, cudaStream_t st) {
+    if (a.ef <= 32) return launch_var<F4, 32>(a, var, st);
+    if (a.ef <= 64) return launch_var<F4, 64>(a, var, st);
+    if (a.ef <= 128) return launch_var<F4, 128>(a, var, st);
+    return launch_var<F4, 256>(a, var, st);
+}
+
+cudaError_t launch_dim(const SearchArgs &a, int var, cudaStream_t st) {
+    switch (a.dim) {
+        case 8: return launch_ef<2>(a, var, st);
+        case 16: return launch_ef<4>(a, var, st);
+        case 32: return launch_ef<8>(a, var, st);
+        case 64: return launch_ef<16>(a, var, st);
+        case 96: return launch_ef<24>(a, var, st);
+        case 128: return launch_ef<32>(a, var, st);
+        case 256: return launch_ef<64>(a, var, st);
+        case 768: return launch_ef<192>(a, var, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+// The queries [q0, q1) of a launch as a launch of their own.
+SearchArgs subrange(const SearchArgs &a, int64_t q0, int64_t q1) {
+    SearchArgs b = a;
+    b.q0 = a.q0 + q0;
+    b.nq = q1 - q0;
+    return b;
+}
+
+// Autotuner: the first launch with at least kTuneMin queries for a (dim,
+// beam) shape times every variant on its own slice of the queries (CUDA
+// events on the launching stream) and keeps the fastest for later launches.
+// Every variant computes the same results, so the choice never changes them.
+constexpr int64_t kTuneMin = 40000;
+constexpr int64_t kTuneSlice = 8000;
+std::mutex g_tune_mu;
+std::map<std::pair<int, int>, int> g_tuned;
+
+int efmax_of(int ef) { return ef <= 32 ? 32 : ef <= 64 ? 64 : ef <= 128 ? 128 : 256; }
+
+}  // namespace
+
+int search_variant_for(int dim, int ef) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned.find({dim, efmax_of(ef)});
+    return it == g_tuned.end() ? -1 : it->second;
+}
+
+namespace {
 
 }  // namespace
 
 cudaError_t launch_search(const SearchArgs &a, cudaStream_t st) {
     if (a.nq <= 0) return cudaSuccess;
-    switch (a.dim) {
-        case 8: return launch_ef<2>(a, st);
-        case 16: return launch_ef<4>(a, st);
-        case 32: return launch_ef<8>(a, st);
-        case 64: return launch_ef<16>(a, st);
-        case 96: return launch_ef<24>(a, st);
-        case 128: return launch_ef<32>(a, st);
-        case 256: return launch_ef<64>(a, st);
-        case 768: return launch_ef<192>(a, st);
-        default: return cudaErrorInvalidValue;
+    if (!search_dim_supported(a.dim)) return cudaErrorInvalidValue;
+    const char *force = getenv("RNSM_SEARCH_VARIANT");
+    if (force && (force[0] == '0' || force[0] == '1')) return launch_dim(a, force[0] - '0', st);
+    const std::pair<int, int> key{a.dim, efmax_of(a.ef)};
+    int var = -1;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tuned.find(key);
+        if (it != g_tuned.end()) var = it->second;
     }
+    if (var >= 0 || a.nq < kTuneMin) return launch_dim(a, var >= 0 ? var : 0, st);
+    // time each variant on its own slice; the slices' results are final
+    float best_ms = 0.f;
+    int best = 0;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return launch_dim(a, 0, st);
+    cudaError_t err = cudaSuccess;
+    for (int v = 0; v < kVariants && err == cudaSuccess; ++v) {
+        const SearchArgs sl = subrange(a, v * kTuneSlice, (v + 1) * kTuneSlice);
+        // the work counter is shared: each slice runs with a zeroed counter
+        err = cudaMemsetAsync(a.work, 0, sizeof(int32_t), st);
+        if (err != cudaSuccess) break;
+        cudaEventRecord(e0, st);
+        err = launch_dim(sl, v, st);
+        cudaEventRecord(e1, st);
+        if (err != cudaSuccess) break;
+        err = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (v == 0 || ms < best_ms) {
+            best_ms = ms;
+            best = v;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (err != cudaSuccess) return err;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tuned[key] = best;
+    }
+    err = cudaMemsetAsync(a.work, 0, sizeof(int32_t), st);
+    if (err != cudaSuccess) return err;
+    return launch_dim(subrange(a, kVariants * kTuneSlice, a.nq), best, st);
 }
 
 bool search_dim_supported(int dim) {

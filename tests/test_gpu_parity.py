@@ -370,3 +370,33 @@ def test_low_precision_merge_equals_fp32(rn, prec):
         assert sa["rechecks"] == 0
         if segs[0].dtype == np.float32 and not (segs[0] == np.rint(segs[0])).all():
             assert sb["rechecks"] > 0       # real-valued data: some decisions re-decided
+
+
+# ---------------------------------------------------------------- autotuner
+
+def test_search_variants_and_autotuned_launch_agree(rn, monkeypatch):
+    # 48k queries trigger the autotuner (slices run with different launch
+    # shapes); every variant must give the same results as the oracle.
+    X = gen.sift_like(20000, 101, d=32)
+    adj, ep = oracle.build_graph(X, 16, 32, 1.2)
+    Q = gen.sift_like(48000, 102, d=32)
+    seeds = np.full((len(Q), 1), ep, np.int32)
+    want, _, _, _, _ = oracle.beam_search(X, adj, Q, seeds, 24, 10)
+    outs = []
+    for force in ("0", "1", None):
+        if force is None:
+            monkeypatch.delenv("RNSM_SEARCH_VARIANT", raising=False)
+        else:
+            monkeypatch.setenv("RNSM_SEARCH_VARIANT", force)
+        ids, _, _ = rn.search(dev(X), dev(adj), dev(Q), dev(seeds), 24, 10)
+        outs.append(host(ids))
+    for o in outs:
+        np.testing.assert_array_equal(o, want)
+
+
+def test_expand_autotuned_on_large_batch(rn):
+    X = gen.sift_like(45000, 103, d=32)
+    adj, _ = oracle.build_graph(X, 16, 32, 1.2)
+    want, _, _, _ = oracle.expand(X, adj, 12)
+    got = rn.expand(dev(X), dev(adj), 12)
+    np.testing.assert_array_equal(host(got), want)
