@@ -402,11 +402,14 @@ SearchArgs subrange(const SearchArgs &a, int64_t q0, int64_t q1) {
 }
 
 // Autotuner: the first launch with at least kTuneMin queries for a (dim,
-// beam) shape times every variant on its own slice of the queries (CUDA
-// events on the launching stream) and keeps the fastest for later launches.
-// Every variant computes the same results, so the choice never changes them.
-constexpr int64_t kTuneMin = 40000;
-constexpr int64_t kTuneSlice = 8000;
+// beam) shape runs every variant on slices of its queries: one untimed
+// warm-up slice each, then two timed slices each in alternating order (CUDA
+// events on the launching stream); the variant with the smallest time per
+// slice is kept for later launches.  Every variant computes the same results,
+// so the choice never changes them.
+constexpr int64_t kTuneWarm = 2000;
+constexpr int64_t kTuneSlice = 10000;
+constexpr int64_t kTuneMin = kVariants * (kTuneWarm + 2 * kTuneSlice) + 10000;
 std::mutex g_tune_mu;
 std::map<std::pair<int, int>, int> g_tuned;
 
@@ -437,40 +440,45 @@ cudaError_t launch_search(const SearchArgs &a, cudaStream_t st) {
         if (it != g_tuned.end()) var = it->second;
     }
     if (var >= 0 || a.nq < kTuneMin) return launch_dim(a, var >= 0 ? var : 0, st);
-    // time each variant on its own slice; the slices' results are final
-    float best_ms = 0.f;
-    int best = 0;
+    // slices of the batch run in turn; their results are final
+    float best_ms[kVariants];
+    for (int v = 0; v < kVariants; ++v) best_ms[v] = 3.4e38f;
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return launch_dim(a, 0, st);
     cudaError_t err = cudaSuccess;
-    for (int v = 0; v < kVariants && err == cudaSuccess; ++v) {
-        const SearchArgs sl = subrange(a, v * kTuneSlice, (v + 1) * kTuneSlice);
-        // the work counter is shared: each slice runs with a zeroed counter
-        err = cudaMemsetAsync(a.work, 0, sizeof(int32_t), st);
-        if (err != cudaSuccess) break;
-        cudaEventRecord(e0, st);
+    int64_t pos = 0;
+    auto run_slice = [&](int v, int64_t len, bool timed) {
+        const SearchArgs sl = subrange(a, pos, pos + len);
+        pos += len;
+        err = cudaMemsetAsync(a.work, 0, sizeof(int32_t), st);  // each slice starts its own count
+        if (err != cudaSuccess) return;
+        if (timed) cudaEventRecord(e0, st);
         err = launch_dim(sl, v, st);
+        if (err != cudaSuccess || !timed) return;
         cudaEventRecord(e1, st);
-        if (err != cudaSuccess) break;
         err = cudaEventSynchronize(e1);
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
-        if (v == 0 || ms < best_ms) {
-            best_ms = ms;
-            best = v;
-        }
-    }
+        if (ms < best_ms[v]) best_ms[v] = ms;
+    };
+    for (int v = 0; v < kVariants && err == cudaSuccess; ++v) run_slice(v, kTuneWarm, false);
+    for (int rep = 0; rep < 2 && err == cudaSuccess; ++rep)
+        for (int k = 0; k < kVariants && err == cudaSuccess; ++k)
+            run_slice(rep == 0 ? k : kVariants - 1 - k, kTuneSlice, true);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (err != cudaSuccess) return err;
+    int best = 0;
+    for (int v = 1; v < kVariants; ++v)
+        if (best_ms[v] < best_ms[best]) best = v;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         g_tuned[key] = best;
     }
     err = cudaMemsetAsync(a.work, 0, sizeof(int32_t), st);
     if (err != cudaSuccess) return err;
-    return launch_dim(subrange(a, kVariants * kTuneSlice, a.nq), best, st);
+    return launch_dim(subrange(a, pos, a.nq), best, st);
 }
 
 bool search_dim_supported(int dim) {
