@@ -78,12 +78,35 @@ __device__ __forceinline__ float chain(float acc, float4 a, float4 b, int metric
     return metric == 0 ? l2_acc(acc, a, b) : ip_acc(acc, a, b);
 }
 
-// Stages float4 columns [d0/4, d0/4 + dc4) of rows [0, nrows4) (rptr) into smem.
-__device__ __forceinline__ void stage(const Smem &s, int nrows4, int d0, int dc4) {
-    for (int e = threadIdx.x; e < nrows4 * dc4; e += kThreads) {
-        const int r = e / dc4, f = e - r * dc4;
-        s.rows[srow4(r) + f] = ldg4(s.rptr[r] + d0 + 4 * f);
+// Stages float4 columns [d0/4, d0/4 + dc4) of rows [0, nrows4) (rptr) into
+// smem; eight loads are issued before their stores so they overlap.
+template <int NT>
+__device__ __forceinline__ void stage_rows(float4 *rows, const float *const *rptr, int nrows4,
+                                           int d0, int dc4) {
+    const int total = nrows4 * dc4;
+    for (int e0 = threadIdx.x; e0 < total; e0 += 8 * NT) {
+        float4 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int e = e0 + u * NT;
+            if (e < total) {
+                const int r = e / dc4, f = e - r * dc4;
+                v[u] = ldg4(rptr[r] + d0 + 4 * f);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int e = e0 + u * NT;
+            if (e < total) {
+                const int r = e / dc4, f = e - r * dc4;
+                rows[srow4(r) + f] = v[u];
+            }
+        }
     }
+}
+
+__device__ __forceinline__ void stage(const Smem &s, int nrows4, int d0, int dc4) {
+    stage_rows<kThreads>(s.rows, s.rptr, nrows4, d0, dc4);
 }
 
 // Block bitonic sort of (pd, pid, prow) by (distance, id) over npad entries.
@@ -472,7 +495,7 @@ struct SmallSmem {
     uint32_t occ[2 * kSmallMax];
 };
 
-__global__ void __launch_bounds__(kSmallThreads) prune_small_kernel(const PruneArgs a, int chunk) {
+__global__ void __launch_bounds__(kSmallThreads, 5) prune_small_kernel(const PruneArgs a, int chunk) {
     __shared__ __align__(16) SmallSmem s;
     __shared__ int64_t sh_i;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -546,10 +569,7 @@ __global__ void __launch_bounds__(kSmallThreads) prune_small_kernel(const PruneA
                 for (int q = 0; q < 4; ++q) acc[t][p][q] = 0.f;
         for (int d0 = 0; d0 < dim; d0 += kDch) {
             const int dc4 = min(kDch, dim - d0) >> 2;
-            for (int e = tid; e < 4 * nB * dc4; e += kSmallThreads) {
-                const int r = e / dc4, f = e - r * dc4;
-                s.rows[srow4(r) + f] = ldg4(s.rptr[r] + d0 + 4 * f);
-            }
+            stage_rows<kSmallThreads>(s.rows, s.rptr, 4 * nB, d0, dc4);
             __syncthreads();
 #pragma unroll
             for (int t = 0; t < kSmallNB; ++t) {
