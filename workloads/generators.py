@@ -15,7 +15,7 @@ Workloads (sizes are parameters so the same recipe serves small parity cases):
 * ``sift_like``     -- 1,000 low-rank Gaussian clusters rounded and clipped to
                        integers 0..255, d=128 (SIFT stand-in).  Every value is
                        an integer, so squared-L2 distances are exact in FP32.
-* ``deep_like``     -- unit-norm d=96 mixture (DEEP stand-in).
+* ``deep_like``     -- unit-norm d=96 mixture of low-rank clusters (DEEP stand-in).
 * ``embed_like``    -- unit-norm d=768 mixture of anisotropic Gaussians
                        (IMAGE embedding stand-in, inner product).
 """
@@ -79,21 +79,35 @@ def _normalise(x: np.ndarray) -> np.ndarray:
     return x / nrm[:, None]
 
 
-def deep_like(n: int, seed: int, d: int = 96, n_comp: int = 1000,
-              sigma: float = 0.35, return_components: bool = False,
+def deep_like(n: int, seed: int, d: int = 96, n_comp: int = 1000, rank: int = 32,
+              scale: float = 0.06, noise: float = 0.01, return_components: bool = False,
               chunk: int = 1 << 18):
-    """Unit-norm mixture: means N(0,I) normalised, isotropic sigma, renormalised.
+    """Unit-norm mixture of low-rank Gaussian clusters (DEEP stand-in).
+
+    x = normalise(mu_j + A_j z + noise * eps): means mu_j ~ N(0, I) normalised,
+    A_j a d x rank matrix of N(0, scale^2) entries, z ~ N(0, I_rank),
+    eps ~ N(0, I_d), uniform component weights.  The defaults put the local
+    intrinsic dimensionality near 19.5 (DEEP in the paper's dataset table);
+    isotropic clusters of the same spread sit near 50 in 96 dimensions.
 
     With ``return_components`` the component index of each row and the
     component means are returned too (used by the cluster partition)."""
     g = _rng(seed)
     means = _normalise(g.standard_normal((n_comp, d)))
+    A = g.standard_normal((n_comp, d, rank)) * scale
     comp_all = g.integers(0, n_comp, size=n)
     out = np.empty((n, d), dtype=np.float32)
     for s in range(0, n, chunk):
         e = min(n, s + chunk)
         comp = comp_all[s:e]
-        x = means[comp] + sigma * g.standard_normal((e - s, d))
+        z = g.standard_normal((e - s, rank))
+        x = means[comp] + noise * g.standard_normal((e - s, d))
+        order = np.argsort(comp, kind="stable")
+        bounds = np.searchsorted(comp[order], np.arange(n_comp + 1))
+        for j in range(n_comp):
+            rows = order[bounds[j]:bounds[j + 1]]
+            if rows.size:
+                x[rows] += z[rows] @ A[j].T
         out[s:e] = _normalise(x).astype(np.float32)
     if return_components:
         return out, comp_all, means
@@ -101,9 +115,11 @@ def deep_like(n: int, seed: int, d: int = 96, n_comp: int = 1000,
 
 
 def embed_like(n: int, seed: int, d: int = 768, n_comp: int = 2000,
-               rank: int = 32, noise: float = 0.02) -> np.ndarray:
+               rank: int = 32, noise: float = 0.013) -> np.ndarray:
     """Unit-norm anisotropic mixture: x = normalise(mu_j + A_j z + noise*eps),
-    A_j a d x rank matrix with singular values 0.3 * 0.9^i, z ~ N(0, I_rank)."""
+    A_j a d x rank matrix with singular values 0.3 * 0.9^i, z ~ N(0, I_rank).
+    The noise level puts the local intrinsic dimensionality near 21 (IMAGE in
+    the paper's dataset table: 21.2)."""
     g = _rng(seed)
     means = _normalise(g.standard_normal((n_comp, d)))
     sv = 0.3 * (0.9 ** np.arange(rank))
