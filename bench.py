@@ -1,12 +1,18 @@
 #!/usr/bin/env python
 """Benchmark of the RNSM merge path: merged vertices/s on one GB300.
 
-Workload: 2 segments x 500,000 vectors, d = 128, SIFT-like integer Gaussian
+Default workload: 2 segments x 500,000 vectors, d = 128, SIFT-like integer Gaussian
 mixture (1,000 clusters, values 0..255), squared L2, R = 32, L = 64,
 alpha = 1.2, FP32.  A step is one rnsm_merge call (expansion, inversion,
 pivot selection, pivot and follower searches, source prune, reverse edges)
 over both segments, inputs resident in HBM.  The input segment graphs are
 built once, untimed, by rnsm_build_segment.
+
+Other workloads (--workload): deep10x2m, ten uneven DEEP-like segments
+(2M rows, d = 96, cluster partition) merged along a MOS plan that is computed
+inside every step; embed4x250k, four 250k-row embedding-like segments
+(d = 768, inner product, R = 64, L = 128) along a MOS plan, where the BF16 /
+FP8 prune tiles matter most.  --scale shrinks a workload for quick runs.
 
 --impl reference times the FP64 CPU oracle instead (host cores, bounded
 sample of the same workload).  Under torchrun every rank runs an independent
@@ -30,13 +36,57 @@ sys.path.insert(0, ROOT)
 
 from workloads import generators as gen  # noqa: E402
 
-WORKLOAD = "sift-like 2x500k d128 L2 R32 L64 alpha1.2"
 METRIC = "merged_vertices_per_s"
 UNIT = "vertices/s"
-R, L, ALPHA, DIM = 32, 64, 1.2, 128
-CPU_SAMPLE = 50_000          # per-segment rows of the oracle's bounded sample
 SEARCH_SRC = os.path.join(ROOT, "paper_2602_17099_gb300", "csrc", "search.cu")
 PROFILE = os.path.join(ROOT, "profiles", "search_kernel_sift2x500k.txt")
+L2_METRIC, IP_METRIC = 0, 1
+
+
+class Workload:
+    """One merge workload: segments, queries, parameters and the host plan.
+
+    ``make(scale, nq)`` returns (segments [list of float32 arrays], queries);
+    ``oracle_scale`` sizes the CPU oracle's bounded sample: the same recipe
+    at that fraction of the full size, with its own plan."""
+
+    def __init__(self, name, desc, dim, R, L, alpha, metric, make, multi, modes, oracle_scale):
+        self.name, self.desc, self.dim = name, desc, dim
+        self.R, self.L, self.alpha, self.metric = R, L, alpha, metric
+        self.make, self.multi, self.modes, self.oracle_scale = make, multi, modes, oracle_scale
+
+
+def _sift(scale, nq, n_per_seg=None):
+    n = n_per_seg if n_per_seg else max(2000, int(500_000 * scale))
+    return gen.sift_case(n_per_seg=n, nq=nq)
+
+
+def _deep(scale, nq):
+    total = max(20_000, int(2_000_000 * scale))
+    sizes = gen.lognormal_sizes(10, total, max(1000, int(50_000 * scale)),
+                                max(4000, int(400_000 * scale)), seed=5)
+    X, comp, means = gen.deep_like(total + nq, 5, return_components=True)
+    parts = gen.cluster_partition(comp[:total], means, sizes, seed=1005)
+    return [X[p_].copy() for p_ in parts], X[total:].copy()
+
+
+def _embed(scale, nq):
+    n = max(2000, int(250_000 * scale))
+    X = gen.embed_like(4 * n + nq, 7)
+    parts = gen.random_partition(4 * n, 4, 1007)
+    return [X[p_].copy() for p_ in parts], X[4 * n:].copy()
+
+
+WORKLOADS = {
+    "sift2x500k": Workload("sift2x500k", "sift-like 2x500k d128 L2 R32 L64 alpha1.2", 128, 32, 64,
+                           1.2, L2_METRIC, _sift, False, ("bf16", "fp8"), 0.1),
+    "deep10x2m": Workload("deep10x2m", "deep-like 10 segments (lognormal 50k-400k, 2M total, "
+                          "cluster partition) d96 L2 R32 L64 alpha1.2, MOS plan", 96, 32, 64,
+                          1.2, L2_METRIC, _deep, True, (), 0.02),
+    "embed4x250k": Workload("embed4x250k", "embedding-like 4x250k d768 IP R64 L128 alpha1.2, "
+                            "MOS plan", 768, 64, 128, 1.2, IP_METRIC, _embed, True,
+                            ("bf16", "fp8"), 0.01),
+}
 
 
 def dist_env():
@@ -123,50 +173,69 @@ class ClockSampler:
 
 # ------------------------------------------------------------- oracle arm
 
-def oracle_sample(n_per_seg=CPU_SAMPLE):
+def centroids_of(segs):
+    return np.stack([s_.mean(axis=0, dtype=np.float64) for s_ in segs]).astype(np.float32)
+
+
+def host_plan(W, segs, planner):
+    """The merge plan: the single-pair default for two segments, else MOS
+    (Algorithm 3) over the segment sizes and centroids."""
+    if not W.multi:
+        return None
+    return planner([len(s_) for s_ in segs], centroids_of(segs))
+
+
+def oracle_sample(W, args):
     """Bounded sample of the workload for the CPU oracle: the same recipe at
-    n_per_seg rows per segment; graphs built by the oracle (untimed)."""
+    ``W.oracle_scale`` of the full size, graphs built by the oracle (untimed)."""
     import oracle
-    segs, _ = gen.sift_case(n_per_seg=n_per_seg, nq=10)
-    gs = [oracle.build_graph(s, R, L, ALPHA) for s in segs]
+    segs, _ = W.make(W.oracle_scale, 10)
+    gs = [oracle.build_graph(s_, W.R, W.L, W.alpha, metric=W.metric) for s_ in segs]
     return oracle, segs, gs
 
 
-def oracle_merge_once(oracle, segs, gs):
+def oracle_merge_once(W, oracle, segs, gs):
     t0 = time.perf_counter()
+    plan = host_plan(W, segs, lambda sz, c: oracle.mos_plan(sz, c))
+    if plan is None:
+        plan = oracle.pair_plan([len(s_) for s_ in segs])
     oracle.rnsm_merge(segs, [g for g, _ in gs], [e for _, e in gs],
-                      oracle.pair_plan([len(s) for s in segs]), R, L, ALPHA)
+                      [(a, b) for a, b, *_ in plan], W.R, W.L, W.alpha, metric=W.metric)
     return time.perf_counter() - t0
 
 
-def cpu_baseline():
-    oracle, segs, gs = oracle_sample()
-    t = oracle_merge_once(oracle, segs, gs)
-    n = sum(len(s) for s in segs)
+def sample_desc(W, segs):
+    return (f"the same recipe at {W.oracle_scale:g} of full size: {len(segs)} segments, "
+            f"{sum(len(s_) for s_ in segs)} rows, FP64 C oracle with OpenMP")
+
+
+def cpu_baseline(W, args):
+    oracle, segs, gs = oracle_sample(W, args)
+    t = oracle_merge_once(W, oracle, segs, gs)
+    n = sum(len(s_) for s_ in segs)
     return {"value": n / t, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
-            "sample": f"2 x {CPU_SAMPLE} rows of the same SIFT-like recipe, one merge, "
-                      f"{t:.2f} s (FP64 C oracle, OpenMP)"}
+            "sample": sample_desc(W, segs) + f", one merge in {t:.2f} s"}
 
 
 def run_reference(args, ws, rank):
     if rank != 0:
         return 0
-    oracle, segs, gs = oracle_sample()
-    n = sum(len(s) for s in segs)
+    W = WORKLOADS[args.workload]
+    oracle, segs, gs = oracle_sample(W, args)
+    n = sum(len(s_) for s_ in segs)
     for _ in range(args.warmup):
-        oracle_merge_once(oracle, segs, gs)
+        oracle_merge_once(W, oracle, segs, gs)
     total = 0.0
     for _ in range(args.steps):
-        total += oracle_merge_once(oracle, segs, gs)
+        total += oracle_merge_once(W, oracle, segs, gs)
     value = n * args.steps / total
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000 * total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample_rows_per_segment": CPU_SAMPLE},
+            "config": {"workload": W.desc, "sample_segments": [len(s_) for s_ in segs]},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.max_threads(),
-                             "kind": "oracle",
-                             "sample": f"2 x {CPU_SAMPLE} rows per step (FP64 C oracle)"},
+                             "kind": "oracle", "sample": sample_desc(W, segs) + " per step"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -198,21 +267,37 @@ def search_profile_traffic():
         return None
 
 
-def recall_at_10(rn, torch, Xd, adj, entry, Q, ef=64):
-    """Tie-tolerant Recall@10 of the merged graph (evaluation only)."""
+def recall_at_10(rn, torch, W, Xd, adj, entry, Q, ef=64):
+    """Tie-tolerant Recall@10 of the merged graph (evaluation only): a returned
+    id counts if its FP64 distance is within the true 10th-NN distance."""
     Qd = torch.from_numpy(Q).cuda()
     seeds = torch.full((len(Q), 1), entry, dtype=torch.int32, device="cuda")
-    ids, _, _ = rn.search(Xd, adj, Qd, seeds, ef, 10)
-    # exact 10-NN distances: integer data, exact in FP32
-    d10 = []
+    ids, _, _ = rn.search(Xd, adj, Qd, seeds, ef, 10, metric=W.metric)
+    Xn = (Xd * Xd).sum(1)
+    hit = 0
     for b in range(0, len(Q), 256):
         q = Qd[b:b + 256]
-        dd = (q * q).sum(1, keepdim=True) + (Xd * Xd).sum(1)[None] - 2.0 * (q @ Xd.T)
-        d10.append(torch.topk(dd, 10, largest=False).values[:, 9])
-    d10 = torch.cat(d10)
-    got = Xd[ids.clamp(min=0).long()]
-    dg = ((got - Qd[:, None, :]) ** 2).sum(-1)
-    hit = ((dg <= d10[:, None]) & (ids >= 0)).sum().item()
+        if W.metric == L2_METRIC:
+            approx = (q * q).sum(1, keepdim=True) + Xn[None] - 2.0 * (q @ Xd.T)
+        else:
+            approx = 1.0 - q @ Xd.T
+        cand = torch.topk(approx, 32, largest=False).indices          # exact re-rank in FP64
+        q64 = q.double()
+        ex = exact = None
+        rows = Xd[cand].double()
+        if W.metric == L2_METRIC:
+            exact = ((rows - q64[:, None, :]) ** 2).sum(-1)
+        else:
+            exact = 1.0 - (rows * q64[:, None, :]).sum(-1)
+        d10 = torch.sort(exact, dim=1).values[:, 9]
+        got = ids[b:b + 256]
+        g = Xd[got.clamp(min=0).long()].double()
+        if W.metric == L2_METRIC:
+            ex = ((g - q64[:, None, :]) ** 2).sum(-1)
+        else:
+            ex = 1.0 - (g * q64[:, None, :]).sum(-1)
+        tol = 1e-9 * d10.abs()[:, None] + 1e-12
+        hit += ((ex <= d10[:, None] + tol) & (got >= 0)).sum().item()
     return hit / (10 * len(Q))
 
 
@@ -222,6 +307,7 @@ def run_ours(args, ws, rank, local):
     from paper_2602_17099_gb300 import build as pkg_build
     from paper_2602_17099_gb300 import rnsm as rn
 
+    W = WORKLOADS[args.workload]
     dist = init_dist(ws)
     if not torch.cuda.is_available():
         raise SystemExit("bench.py needs a CUDA device (there is no CPU path)")
@@ -231,21 +317,30 @@ def run_ours(args, ws, rank, local):
     barrier(dist)
     rn.lib()
 
-    n_per = args.n_per_seg
-    segs, Q = gen.sift_case(n_per_seg=n_per, nq=args.recall_queries)
-    N = sum(len(s) for s in segs)
-    vd = [torch.from_numpy(s).cuda() for s in segs]
+    if W.name == "sift2x500k":
+        segs, Q = _sift(args.scale, args.recall_queries, n_per_seg=args.n_per_seg)
+    else:
+        segs, Q = W.make(args.scale, args.recall_queries)
+    N = sum(len(s_) for s_ in segs)
+    cen = centroids_of(segs)
+    vd = [torch.from_numpy(s_).cuda() for s_ in segs]
     t0 = time.perf_counter()
-    graphs = [rn.build_segment(v, R, L, ALPHA) for v in vd]
+    graphs = [rn.build_segment(v, W.R, W.L, W.alpha, metric=W.metric) for v in vd]
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
     tsegs = [(v, g, e) for v, (g, e) in zip(vd, graphs)]
-    p = rn.params(R, L, ALPHA)
-    out = torch.empty((N, R), dtype=torch.int32, device="cuda")
+    sizes = [len(s_) for s_ in segs]
+
+    def plan_now():
+        # MOS runs inside the timed step (a host planner over sizes and centroids)
+        return rn.mos_plan(sizes, cen) if W.multi else None
+
+    p = rn.params(W.R, W.L, W.alpha, metric=W.metric)
+    out = torch.empty((N, W.R), dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
 
     for _ in range(args.warmup):
-        rn.merge(tsegs, p, out=out)
+        rn.merge(tsegs, p, plan=plan_now(), out=out)
     torch.cuda.synchronize()
 
     gpu_id = torch.cuda.get_device_properties(local).uuid
@@ -256,10 +351,12 @@ def run_ours(args, ws, rank, local):
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     stats = []
+    plan_used = None
     ev0.record(stream)
     for _ in range(args.steps):
         torch.cuda.nvtx.range_push("rnsm_merge")
-        _, st = rn.merge(tsegs, p, out=out)
+        plan_used = plan_now()
+        _, st = rn.merge(tsegs, p, plan=plan_used, out=out)
         torch.cuda.nvtx.range_pop()
         stats.append(st)
     ev1.record(stream)
@@ -274,13 +371,15 @@ def run_ours(args, ws, rank, local):
     # library's CUDA events on the launching stream and its NDC counters
     s_bytes = s_ms = 0.0
     launches = 0
+    n_search_launches = 0
     for st in stats:
         for i, ph in ((0, 1), (1, 4), (2, 5)):
-            s_bytes += (st["search_ndc"][i] * DIM * 4 + st["search_exp"][i] * R * 4 +
-                        st["search_queries"][i] * DIM * 4)
+            s_bytes += (st["search_ndc"][i] * W.dim * 4 + st["search_exp"][i] * W.R * 4 +
+                        st["search_queries"][i] * W.dim * 4)
             s_ms += st["phase_ms"][ph]
         launches += st["launches"]
-    n_search_launches = 3 * len(stats)
+        # one multi-job launch each for S1, S4 and S5 (every pair of the plan)
+        n_search_launches += 3
     peaks = {}
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -289,14 +388,14 @@ def run_ours(args, ws, rank, local):
         pass
     peak = float(peaks.get("hbm_gbs", 6800.0))
     achieved = (s_bytes / n_search_launches) / (s_ms / n_search_launches / 1000.0) / 1e9
-    traffic = search_profile_traffic()
+    traffic = search_profile_traffic() if W.name == "sift2x500k" else None
     roofline = {"bound": "hbm", "kernel": "search_kernel (S1+S4+S5 launches)",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
                 "traffic": traffic,
                 "algorithmic_bytes_per_launch": s_bytes / n_search_launches,
                 "avg_launch_ms": s_ms / n_search_launches}
-    phases = ["validate_init", "S1_expand", "S2_invert", "S3_pivots_host", "S4_pivot_search",
+    phases = ["validate_init", "S1_expand", "S2_invert", "S3_pivots", "S4_pivot_search",
               "S5_follower_search", "S6_source_prune", "S7_reverse_edges"]
     phase_ms = {nm: sum(st["phase_ms"][i] for st in stats) / len(stats)
                 for i, nm in enumerate(phases)}
@@ -305,18 +404,19 @@ def run_ours(args, ws, rank, local):
     # cores + FP32 re-decisions); their graphs must equal the FP32 graph
     modes = {}
     ref_out = out.clone()
-    for name, prec in (("bf16", rn.BF16), ("fp8", rn.FP8)):
-        pq = rn.params(R, L, ALPHA, prec=prec)
+    for name in W.modes:
+        prec = {"bf16": rn.BF16, "fp8": rn.FP8}[name]
+        pq = rn.params(W.R, W.L, W.alpha, metric=W.metric, prec=prec)
         oq = torch.empty_like(out)
         for _ in range(2):
-            rn.merge(tsegs, pq, out=oq)
+            rn.merge(tsegs, pq, plan=plan_now(), out=oq)
         torch.cuda.synchronize()
         q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         qs = []
         nq = max(3, args.steps // 2)
         q0.record(stream)
         for _ in range(nq):
-            _, st = rn.merge(tsegs, pq, out=oq)
+            _, st = rn.merge(tsegs, pq, plan=plan_now(), out=oq)
             qs.append(st)
         q1.record(stream)
         torch.cuda.synchronize()
@@ -324,6 +424,12 @@ def run_ours(args, ws, rank, local):
         modes[name] = {"ms_per_step": qms, "value": N / (qms / 1000.0), "unit": UNIT,
                        "identical_to_fp32": bool(torch.equal(oq, ref_out)),
                        "rechecks_per_step": qs[-1]["rechecks"],
+                       # sampled owner distances: tile and FP32 vs FP64, bound use
+                       "distance_error": {
+                           "tile_vs_fp64_max_rel": qs[-1]["tile_error"][0],
+                           "fp32_vs_fp64_max_rel": qs[-1]["tile_error"][1],
+                           "tile_vs_fp32_max_share_of_bound": qs[-1]["tile_error"][2],
+                           "samples": int(qs[-1]["tile_error"][3])},
                        "prune_ms": round(sum(st["phase_ms"][6] + st["phase_ms"][7]
                                              for st in qs) / nq, 3)}
     modes["fp32"] = {"ms_per_step": ms_max / args.steps,
@@ -332,7 +438,7 @@ def run_ours(args, ws, rank, local):
     # end to end through the public API with host buffers
     pin_v = [s_.cpu().pin_memory() for s_ in vd]
     pin_g = [g.cpu().pin_memory() for g, _ in graphs]
-    pin_out = torch.empty((N, R), dtype=torch.int32).pin_memory()
+    pin_out = torch.empty((N, W.R), dtype=torch.int32).pin_memory()
     dv = [torch.empty_like(v) for v in vd]
     dg = [torch.empty_like(g) for g, _ in graphs]
     h2d = sum(t.numel() * t.element_size() for t in pin_v + pin_g)
@@ -346,7 +452,8 @@ def run_ours(args, ws, rank, local):
             a.copy_(b, non_blocking=True)
         for a, b in zip(dg, pin_g):
             a.copy_(b, non_blocking=True)
-        rn.merge([(v, g, e) for v, g, (_, e) in zip(dv, dg, graphs)], p, out=out)
+        rn.merge([(v, g, e) for v, g, (_, e) in zip(dv, dg, graphs)], p, plan=plan_now(),
+                 out=out)
         pin_out.copy_(out, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
@@ -357,25 +464,29 @@ def run_ours(args, ws, rank, local):
     rec = None
     if rank == 0 and args.recall_queries > 0:
         Xd = torch.cat(vd)
-        big = 0 if len(segs[0]) >= len(segs[1]) else 1
-        entry = graphs[big][1] + (0 if big == 0 else len(segs[0]))
+        big = int(np.argmax(sizes))
+        entry = graphs[big][1] + sum(sizes[:big])
         rec = {"ef": 64, "queries": args.recall_queries,
-               "value": recall_at_10(rn, torch, Xd, out, entry, Q)}
+               "value": recall_at_10(rn, torch, W, Xd, out, entry, Q)}
 
     base = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        base = cpu_baseline()
+        base = cpu_baseline(W, args)
 
     if rank == 0:
+        vec_bytes = sum(v.numel() * 4 for v in vd)
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
                 "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic",
-                "config": {"workload": WORKLOAD, "segments": [len(s) for s in segs],
-                           "dim": DIM, "R": R, "L": L, "alpha": ALPHA, "precision": "fp32",
+                "config": {"workload": W.desc, "segments": sizes,
+                           "dim": W.dim, "R": W.R, "L": W.L, "alpha": W.alpha,
+                           "metric": "l2" if W.metric == L2_METRIC else "ip",
+                           "precision": "fp32",
+                           "plan": None if plan_used is None else [list(e[:2]) for e in plan_used],
                            "parallelism": "replicas" if ws > 1 else "single",
-                           "l2": "inputs larger than L2 (512 MB of vectors)",
+                           "l2": f"inputs larger than L2 ({vec_bytes >> 20} MB of vectors)",
                            "input_graph_build_s": round(build_s, 3),
                            "phase_ms": {k: round(v, 3) for k, v in phase_ms.items()},
                            "recall_at_10": rec,
@@ -397,7 +508,11 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--n-per-seg", type=int, default=500_000)
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="sift2x500k")
+    ap.add_argument("--scale", type=float, default=1.0,
+                    help="size factor of the workload (1.0 = full size)")
+    ap.add_argument("--n-per-seg", type=int, default=0,
+                    help="sift2x500k only: rows per segment (overrides --scale)")
     ap.add_argument("--recall-queries", type=int, default=1000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

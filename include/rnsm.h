@@ -10,7 +10,14 @@
  *   that the library grows on demand and keeps until rnsm_release_workspace()
  *   or process exit.
  * - Vectors are row-major float32, rows contiguous, 16-byte aligned (dim must
- *   be a multiple of 4).  Graphs are int32 adjacency rows padded with -1.
+ *   be a multiple of 4, at most 1024).  Calls that search (rnsm_search,
+ *   rnsm_expand, rnsm_build_segment, rnsm_merge) need a dimension the search
+ *   kernel is built for: 8, 16, 32, 64, 96, 128, 256 or 768; the prune,
+ *   reverse-edge and medoid calls take any.  The BF16 / FP8 prune tiles need
+ *   dim a multiple of 16 (BF16) or 32 (FP8); other dimensions run the FP32
+ *   kernels.  Graphs are int32 adjacency rows padded with -1.
+ * - Timeouts: the tensor-core prune waits on its MMAs for at most one second;
+ *   a wait that runs out ends the call with RNSM_ETIMEOUT, the context usable.
  * - Distances (native, never square-rooted): RNSM_METRIC_L2 = squared
  *   Euclidean distance (orders exactly like the paper's delta, notation table
  *   of Section 2); RNSM_METRIC_IP = 1 - <x, y> for unit-norm embeddings.
@@ -121,6 +128,12 @@ typedef struct {
     int64_t search_ndc[3]; /* NDC of S1, S4, S5 */
     int64_t search_exp[3]; /* expansions of S1, S4, S5 */
     int64_t search_queries[3]; /* queries of S1, S4, S5 */
+    /* BF16 / FP8 modes: distance error of the tensor-core prune tiles, sampled
+     * on the owner distances of every 64th owner: [0] max |d~ - d64| / d64
+     * (tile vs FP64), [1] max |d32 - d64| / d64 (the FP32 distance vs FP64),
+     * [2] max |d~ - d32| / B (the share of its error bound B the tile used),
+     * [3] number of distances sampled.  Zero in FP32 mode. */
+    double tile_error[4];
 } rnsm_stats;
 
 /*

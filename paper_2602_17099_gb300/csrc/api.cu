@@ -102,6 +102,7 @@ struct Ctl {
     unsigned long long *stats;  // per search slot s: [2s] ndc, [2s+1] expansions
     unsigned long long *ecount;
     unsigned long long *rechecks;  // prune decisions re-decided in FP32
+    unsigned int *tile_err;  // [4] tile error statistics (see rnsm_stats)
     int32_t *scratch_i;      // misc int
 };
 
@@ -114,16 +115,20 @@ struct QuantBufs {
 
 void take_quant(Bump &b, int64_t n, int32_t dim, int32_t prec, QuantBufs &qb) {
     qb.prec = prec;
+    qb.q = nullptr;
     if (prec == 0) return;
+    if (prune_tc_terms(dim, prec) == 2) return;   // the split tile stages the FP32 rows
     qb.q = b.take<char>((size_t)n * dim * (prec == 2 ? 1 : 2));
     qb.scale = b.take<float>(n);
     qb.err = b.take<float>(n);
     qb.norm = b.take<float>(n);
 }
 
-void apply_quant(PruneArgs &a, const QuantBufs *qb, unsigned long long *rechecks) {
+void apply_quant(PruneArgs &a, const QuantBufs *qb, unsigned long long *rechecks,
+                 unsigned int *tile_err = nullptr) {
     a.rechecks = rechecks;
     if (!qb || qb->prec == 0) return;
+    a.tile_err = tile_err;
     a.prec = qb->prec;
     a.qrows = qb->q;
     a.qscale = qb->scale;
@@ -141,6 +146,7 @@ void take_ctl(Bump &b, Ctl &c, int64_t max_owners = 0) {
     c.stats = b.take<unsigned long long>(8);
     c.ecount = b.take<unsigned long long>(1);
     c.rechecks = b.take<unsigned long long>(1);
+    c.tile_err = b.take<unsigned int>(4);
     c.scratch_i = b.take<int32_t>(4);
 }
 
@@ -148,6 +154,7 @@ rnsm_status ctl_reset(const Ctl &c, cudaStream_t st) {
     CK(cudaMemsetAsync(c.err, 0, sizeof(int32_t), st));
     CK(cudaMemsetAsync(c.stats, 0, 8 * sizeof(unsigned long long), st));
     CK(cudaMemsetAsync(c.rechecks, 0, sizeof(unsigned long long), st));
+    CK(cudaMemsetAsync(c.tile_err, 0, 4 * sizeof(unsigned int), st));
     return RNSM_OK;
 }
 
@@ -191,12 +198,14 @@ rnsm_status resolve_params(const rnsm_params *in, rnsm_params &p) {
     return RNSM_OK;
 }
 
-rnsm_status check_vecs(const float *v, int64_t n, int32_t dim) {
+// need_search: the call runs the beam search, whose kernels exist for a set of dimensions
+rnsm_status check_vecs(const float *v, int64_t n, int32_t dim, bool need_search = true) {
     if (!v) return fail(RNSM_EINVAL, "vector pointer is NULL");
     if (n < 1) return fail(RNSM_EINVAL, "n=%lld must be >= 1", (long long)n);
     if (n >= INT32_MAX) return fail(RNSM_EINVAL, "n must be < 2^31");
     if (dim < 4 || (dim & 3)) return fail(RNSM_EINVAL, "dim=%d must be a positive multiple of 4", dim);
-    if (!search_dim_supported(dim)) return fail(RNSM_EINVAL, "dim=%d has no search kernel", dim);
+    if (need_search && !search_dim_supported(dim))
+        return fail(RNSM_EINVAL, "dim=%d has no search kernel", dim);
     if (dim > 1024) return fail(RNSM_EINVAL, "dim=%d above 1024", dim);
     if (!aligned16(v)) return fail(RNSM_EINVAL, "vectors must be 16-byte aligned");
     return RNSM_OK;
@@ -303,7 +312,7 @@ rnsm_status reverse_into(const SegTable &tab, int32_t dim, const rnsm_params &p,
     a.csr_max = csr_max;
     a.out = lists;
     a.err = c.err;
-    apply_quant(a, qb, c.rechecks);
+    apply_quant(a, qb, c.rechecks, c.tile_err);
     return run_prune(a, c.work + 6, c, st);
 }
 
@@ -523,7 +532,7 @@ rnsm_status rnsm_prune(const float *vecs, int64_t n, int32_t dim, const int32_t 
                        void *stream) {
     std::lock_guard<std::mutex> lk(g_mu);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    TRY(check_vecs(vecs, n, dim));
+    TRY(check_vecs(vecs, n, dim, false));
     if (nv < 0 || (nv > 0 && (!owners || !out)) || w_len < 0 || w_len > 2048 ||
         (w_len > 0 && nv > 0 && !pool))
         return fail(RNSM_EINVAL, "bad owners, pool or output");
@@ -531,7 +540,7 @@ rnsm_status rnsm_prune(const float *vecs, int64_t n, int32_t dim, const int32_t 
     if (!(std::isfinite(alpha) && alpha >= 0.f)) return fail(RNSM_EINVAL, "bad alpha");
     if (metric != 0 && metric != 1) return fail(RNSM_EINVAL, "unknown metric");
     if (prec < RNSM_PREC_FP32 || prec > RNSM_PREC_FP8) return fail(RNSM_EINVAL, "unknown precision");
-    const int32_t qprec = prune_tc_supported(dim, prec) ? prec : 0;  // else the FP32 kernels
+    const int32_t qprec = prune_tc_terms(dim, prec) ? prec : 0;  // else the FP32 kernels
     if (nv == 0) return RNSM_OK;
     Bump b;
     Ctl c;
@@ -567,7 +576,7 @@ rnsm_status rnsm_prune(const float *vecs, int64_t n, int32_t dim, const int32_t 
     a.out = out;
     a.out_by_index = 1;
     a.err = c.err;
-    if (qprec) CK(launch_quantize(tab, n, dim, qprec, qb.q, qb.scale, qb.err, qb.norm, st));
+    if (qb.q) CK(launch_quantize(tab, n, dim, qprec, qb.q, qb.scale, qb.err, qb.norm, st));
     apply_quant(a, &qb, c.rechecks);
     TRY(run_prune(a, c.work + 8, c, st));
     TRY(check_err_word(c, st));
@@ -579,7 +588,7 @@ rnsm_status rnsm_reverse_edges(const float *vecs, int64_t n, int32_t dim, int32_
                                float alpha, int32_t metric, void *stream) {
     std::lock_guard<std::mutex> lk(g_mu);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    TRY(check_vecs(vecs, n, dim));
+    TRY(check_vecs(vecs, n, dim, false));
     if (!lists || R < 1 || R > 64 || ne < 0 || (ne > 0 && (!eu || !ev)))
         return fail(RNSM_EINVAL, "bad arguments");
     if (!(std::isfinite(alpha) && alpha >= 0.f)) return fail(RNSM_EINVAL, "bad alpha");
@@ -617,7 +626,7 @@ rnsm_status rnsm_medoid(const float *vecs, int64_t n, int32_t dim, int32_t metri
                         int32_t *out_entry, void *stream) {
     std::lock_guard<std::mutex> lk(g_mu);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    TRY(check_vecs(vecs, n, dim));
+    TRY(check_vecs(vecs, n, dim, false));
     if (!out_entry) return fail(RNSM_EINVAL, "out_entry is NULL");
     Bump b;
     Ctl c;
@@ -734,104 +743,138 @@ rnsm_status rnsm_build_segment(const float *vecs, int64_t n, int32_t dim, const 
 }
 
 // ------------------------------------------------------------------ merge
+//
+// Execution of a plan (pattern: batched pairs).  Searches read only the
+// frozen input graphs, so every search of every plan edge is independent of
+// the list updates: the merge runs
+//   S1 for every source segment of the plan in one multi-job launch,
+//   S2 and S3 per source,
+//   S4 for every plan edge of a group in one multi-job launch, then S5 alike,
+//   S6 and S7 per plan edge in plan order (they update the lists),
+// where a group is a run of consecutive plan edges whose result tables fit
+// the result budget (all edges of a plan, unless the segments are huge).
+// The results equal those of running Algorithm 2 edge by edge.
 
 namespace {
 
-struct PairNeeds {
-    int64_t ns, nt;
-};
+constexpr size_t kResBudgetBytes = size_t(4) << 30;   // search results of one group
 
 struct MergeBufs {
-    int32_t *nplus, *rk_keys, *rk_vals, *rk_ids, *rk_cursor;
+    int32_t *nplus;                        // [N * k_plus], rows of segment s at off[s]
+    int32_t *rk_keys, *rk_vals, *rk_ids, *rk_cursor;
     int64_t *rk_offs;
     void *rk_scan;
     size_t rk_scan_bytes;
-    int32_t *pivots, *followers, *pivot_of, *res, *eu, *ev;
+    int32_t *pivot_of, *pivots, *followers;   // [N] each, segment s at off[s]
     void *piv_tmp;
+    int32_t *res;                          // [res_rows * L]
+    int32_t *eu, *ev;
+    SearchJob *jobs1, *jobs4, *jobs5;
     RevBufs rev;
     QuantBufs qb;
 };
 
-void carve_merge(Bump &b, const rnsm_params &p, int64_t ns_max, int64_t nt_max, int64_t n_all,
-                 int32_t dim, int32_t qprec, Ctl &c, MergeBufs &m) {
-    take_ctl(b, c, ns_max > nt_max ? ns_max : nt_max);
-    m.nplus = b.take<int32_t>(ns_max * p.k_plus);
-    m.rk_keys = b.take<int32_t>(ns_max * p.k_rev);
-    m.rk_vals = b.take<int32_t>(ns_max * p.k_rev);
-    m.rk_ids = b.take<int32_t>(ns_max * p.k_rev);
-    m.rk_cursor = b.take<int32_t>(ns_max);
-    m.rk_offs = b.take<int64_t>(ns_max + 1);
-    m.rk_scan_bytes = bucket_scan_tmp_bytes(ns_max);
+void carve_merge(Bump &b, const rnsm_params &p, int64_t nmax, int64_t n_all, int64_t res_rows,
+                 int32_t n_jobs, int32_t dim, int32_t qprec, Ctl &c, MergeBufs &m) {
+    take_ctl(b, c, nmax);
+    m.nplus = b.take<int32_t>(n_all * p.k_plus);
+    m.rk_keys = b.take<int32_t>(nmax * p.k_rev);
+    m.rk_vals = b.take<int32_t>(nmax * p.k_rev);
+    m.rk_ids = b.take<int32_t>(nmax * p.k_rev);
+    m.rk_cursor = b.take<int32_t>(nmax);
+    m.rk_offs = b.take<int64_t>(nmax + 1);
+    m.rk_scan_bytes = bucket_scan_tmp_bytes(nmax);
     m.rk_scan = b.take<char>(m.rk_scan_bytes);
-    m.pivots = b.take<int32_t>(ns_max);
-    m.followers = b.take<int32_t>(ns_max);
-    m.pivot_of = b.take<int32_t>(ns_max);
-    m.piv_tmp = b.take<char>(pivot_tmp_bytes(ns_max));
-    m.res = b.take<int32_t>(ns_max * p.L);
-    m.eu = b.take<int32_t>(ns_max * p.R);
-    m.ev = b.take<int32_t>(ns_max * p.R);
-    take_rev(b, nt_max, ns_max * p.R, m.rev);
+    m.pivot_of = b.take<int32_t>(n_all);
+    m.pivots = b.take<int32_t>(n_all);
+    m.followers = b.take<int32_t>(n_all);
+    m.piv_tmp = b.take<char>(pivot_tmp_bytes(nmax));
+    m.res = b.take<int32_t>(res_rows * p.L);
+    m.eu = b.take<int32_t>(nmax * p.R);
+    m.ev = b.take<int32_t>(nmax * p.R);
+    m.jobs1 = b.take<SearchJob>(n_jobs + 1);
+    m.jobs4 = b.take<SearchJob>(n_jobs + 1);
+    m.jobs5 = b.take<SearchJob>(n_jobs + 1);
+    take_rev(b, nmax, nmax * p.R, m.rev);
     take_quant(b, n_all, dim, qprec, m.qb);
 }
 
-// CUDA events at the step boundaries of one plan edge (S1 .. S7).
-struct PhaseClock {
-    cudaEvent_t ev[9] = {};
-    bool ok = true;
-    PhaseClock() {
-        for (auto &e : ev) ok = ok && cudaEventCreate(&e) == cudaSuccess;
+// Rows of result table needed by the largest group of the plan.
+int64_t plan_res_rows(const rnsm_segment *segs, const std::vector<PlanEdge> &pl, int32_t L) {
+    const int64_t budget = (int64_t)(kResBudgetBytes / ((size_t)L * sizeof(int32_t)));
+    int64_t best = 0, cur = 0;
+    for (const PlanEdge &e : pl) {
+        const int64_t ns = segs[e.src].n;
+        if (cur > 0 && cur + ns > budget) cur = 0;
+        cur += ns;
+        best = cur > best ? cur : best;
     }
-    ~PhaseClock() {
-        for (auto &e : ev)
-            if (e) cudaEventDestroy(e);
+    return best;
+}
+
+// CUDA events around the phases of a merge; elapsed times are summed per
+// phase after the final synchronisation.
+struct PhaseTimer {
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> spans;
+    cudaStream_t st;
+    explicit PhaseTimer(cudaStream_t s) : st(s) {}
+    ~PhaseTimer() {
+        for (auto &sp : spans) {
+            cudaEventDestroy(sp.second.first);
+            cudaEventDestroy(sp.second.second);
+        }
     }
-    void mark(int i, cudaStream_t st) {
-        if (ok) cudaEventRecord(ev[i], st);
+    int begin(int phase) {
+        cudaEvent_t a = nullptr, z = nullptr;
+        if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&z) != cudaSuccess) {
+            if (a) cudaEventDestroy(a);
+            cudaGetLastError();
+            return -1;
+        }
+        cudaEventRecord(a, st);
+        spans.push_back({phase, {a, z}});
+        return (int)spans.size() - 1;
     }
-    // after a stream sync: phase_ms[i + shift] += time from mark i to mark i + 1
-    void add(double *phase_ms, int lo, int hi, int shift) {
-        if (!ok) return;
-        for (int i = lo; i < hi; ++i) {
+    void end(int idx) {
+        if (idx >= 0) cudaEventRecord(spans[(size_t)idx].second.second, st);
+    }
+    void add(double *phase_ms) const {
+        for (const auto &sp : spans) {
             float ms = 0.f;
-            if (cudaEventElapsedTime(&ms, ev[i], ev[i + 1]) == cudaSuccess) phase_ms[i + shift] += ms;
+            if (cudaEventElapsedTime(&ms, sp.second.first, sp.second.second) == cudaSuccess)
+                phase_ms[sp.first] += ms;
         }
     }
 };
 
-struct SrcCache {
-    bool done = false;
-    int64_t np = 0, nf = 0;
-    std::vector<int32_t> pivot_of, pivots, followers;  // host copies (device S3 keeps its own)
-    bool on_device = false;
-};
-
-}  // namespace
-
-size_t rnsm_workspace_size(const rnsm_segment *segs, int32_t m, const rnsm_params *pin) {
-    rnsm_params p;
-    if (resolve_params(pin, p) != RNSM_OK || !segs || m < 1) return 0;
-    int64_t nmax = 0, nall = 0;
-    for (int32_t s = 0; s < m; ++s) {
-        nmax = segs[s].n > nmax ? segs[s].n : nmax;
-        nall += segs[s].n;
-    }
-    const int32_t qprec = prune_tc_supported(segs[0].dim, p.prec) ? p.prec : 0;
-    Bump b;
-    Ctl c;
-    MergeBufs mb;
-    carve_merge(b, p, nmax, nmax, nall, segs[0].dim, qprec, c, mb);
-    return b.off;
+SearchJob make_job(const rnsm_segment &T, const float *qvecs, const int32_t *qidx,
+                   int32_t *out_ids, int64_t q_begin) {
+    SearchJob j;
+    std::memset(&j, 0, sizeof(j));
+    j.base = T.vecs;
+    j.adj = T.adj;
+    j.n_base = T.n;
+    j.r_in = T.r_in;
+    j.seed_const = T.entry;
+    j.qvecs = qvecs;
+    j.qidx = qidx;
+    j.out_ids = out_ids;
+    j.q_begin = q_begin;
+    return j;
 }
 
-rnsm_status rnsm_merge(const rnsm_segment *segs, int32_t m, const rnsm_params *pin,
-                       const mos_edge *plan, int32_t n_plan, int32_t *out_adj, void *stream,
-                       rnsm_stats *stats) {
-    const auto t0 = std::chrono::steady_clock::now();
-    rnsm_params p;
-    TRY(resolve_params(pin, p));
-    TRY(check_segments(segs, m, p.R));
-    if (!out_adj) return fail(RNSM_EINVAL, "out_adj is NULL");
-    std::vector<PlanEdge> pl;
+rnsm_status upload_jobs(std::vector<SearchJob> &jobs, int64_t total, SearchJob *dev,
+                        cudaStream_t st) {
+    SearchJob end;
+    std::memset(&end, 0, sizeof(end));
+    end.q_begin = total;   // sentinel
+    jobs.push_back(end);
+    CK(cudaMemcpyAsync(dev, jobs.data(), jobs.size() * sizeof(SearchJob), cudaMemcpyHostToDevice, st));
+    return RNSM_OK;
+}
+
+rnsm_status resolve_plan(const rnsm_segment *segs, int32_t m, const mos_edge *plan, int32_t n_plan,
+                         std::vector<PlanEdge> &pl) {
     if (plan) {
         if (n_plan < 0) return fail(RNSM_EINVAL, "n_plan < 0");
         for (int32_t i = 0; i < n_plan; ++i) {
@@ -847,13 +890,48 @@ rnsm_status rnsm_merge(const rnsm_segment *segs, int32_t m, const rnsm_params *p
     } else if (m > 2) {
         return fail(RNSM_EINVAL, "m > 2 needs a plan (mos_plan)");
     }
+    return RNSM_OK;
+}
+
+}  // namespace
+
+size_t rnsm_workspace_size(const rnsm_segment *segs, int32_t m, const rnsm_params *pin) {
+    rnsm_params p;
+    if (resolve_params(pin, p) != RNSM_OK || !segs || m < 1) return 0;
+    int64_t nmax = 0, nall = 0;
+    for (int32_t s = 0; s < m; ++s) {
+        nmax = segs[s].n > nmax ? segs[s].n : nmax;
+        nall += segs[s].n;
+    }
+    const int32_t qprec = prune_tc_terms(segs[0].dim, p.prec) ? p.prec : 0;
+    // a plan of any order: at most m(m-1) edges, results of at most the budget
+    const int64_t budget = (int64_t)(kResBudgetBytes / ((size_t)p.L * sizeof(int32_t)));
+    int64_t res_rows = nall * (m > 1 ? m - 1 : 1);
+    if (res_rows > budget) res_rows = budget > nmax ? budget : nmax;
+    Bump b;
+    Ctl c;
+    MergeBufs mb;
+    carve_merge(b, p, nmax, nall, res_rows, m * (m > 1 ? m - 1 : 1), segs[0].dim, qprec, c, mb);
+    return b.off;
+}
+
+rnsm_status rnsm_merge(const rnsm_segment *segs, int32_t m, const rnsm_params *pin,
+                       const mos_edge *plan, int32_t n_plan, int32_t *out_adj, void *stream,
+                       rnsm_stats *stats) {
+    const auto t0 = std::chrono::steady_clock::now();
+    rnsm_params p;
+    TRY(resolve_params(pin, p));
+    TRY(check_segments(segs, m, p.R));
+    if (!out_adj) return fail(RNSM_EINVAL, "out_adj is NULL");
+    std::vector<PlanEdge> pl;
+    TRY(resolve_plan(segs, m, plan, n_plan, pl));
     std::lock_guard<std::mutex> lk(g_mu);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const long long launches0 = launches_so_far();
     double phase_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     int64_t queries[3] = {0, 0, 0};
-    PhaseClock clk;
-    clk.mark(0, st);
+    PhaseTimer tm(st);
+    const int t_init = tm.begin(0);
     const int32_t dim = segs[0].dim;
     SegTable tab;
     std::memset(&tab, 0, sizeof(tab));
@@ -866,13 +944,15 @@ rnsm_status rnsm_merge(const rnsm_segment *segs, int32_t m, const rnsm_params *p
         nmax = segs[s].n > nmax ? segs[s].n : nmax;
     }
     tab.off[m] = off;
-    const int32_t qprec = prune_tc_supported(dim, p.prec) ? p.prec : 0;  // else FP32 kernels
+    const int32_t qprec = prune_tc_terms(dim, p.prec) ? p.prec : 0;  // else FP32 kernels
+    const int64_t res_rows = plan_res_rows(segs, pl, p.L);
+    const int32_t n_jobs = (int32_t)pl.size() > m ? (int32_t)pl.size() : m;
     Bump b;
     Ctl c;
     MergeBufs mb;
-    carve_merge(b, p, nmax, nmax, off, dim, qprec, c, mb);
+    carve_merge(b, p, nmax, off, res_rows, n_jobs, dim, qprec, c, mb);
     TRY(ws_acquire(b.off, b));
-    carve_merge(b, p, nmax, nmax, off, dim, qprec, c, mb);
+    carve_merge(b, p, nmax, off, res_rows, n_jobs, dim, qprec, c, mb);
     TRY(ctl_reset(c, st));
     for (int32_t s = 0; s < m; ++s)
         TRY(validate_on_device(segs[s].vecs, segs[s].n, dim, segs[s].adj, segs[s].r_in, c, st));
@@ -880,222 +960,249 @@ rnsm_status rnsm_merge(const rnsm_segment *segs, int32_t m, const rnsm_params *p
     for (int32_t s = 0; s < m; ++s)
         CK(launch_init_lists(segs[s].adj, segs[s].n, segs[s].r_in, (int32_t)tab.off[s],
                              out_adj + tab.off[s] * p.R, p.R, st));
-    if (qprec)  // BF16 / E4M3 copies of every row for the tensor-core prune tiles
+    if (mb.qb.q)  // BF16 / E4M3 copies of every row for the one-term tensor-core tiles
         CK(launch_quantize(tab, off, dim, qprec, mb.qb.q, mb.qb.scale, mb.qb.err, mb.qb.norm, st));
-    clk.mark(1, st);
-    CK(cudaStreamSynchronize(st));
-    clk.add(phase_ms, 0, 1, 0);
+    tm.end(t_init);
 
-    std::vector<SrcCache> cache((size_t)m);
+    const int32_t ks = p.ef_slide < p.L ? p.ef_slide : p.L;
+    const bool cm = (p.flags & RNSM_FLAG_CM) != 0;
+    std::vector<int32_t> srcs;            // source segments in order of first use
+    std::vector<char> is_src((size_t)m, 0);
+    for (const PlanEdge &e : pl)
+        if (!is_src[(size_t)e.src]) {
+            is_src[(size_t)e.src] = 1;
+            srcs.push_back(e.src);
+        }
+    std::vector<int64_t> np((size_t)m, 0), nf((size_t)m, 0);
     double host_s = 0.0;
     int64_t n_piv = 0, n_fol = 0;
     unsigned long long rev_total = 0;
-    const int32_t ks = p.ef_slide < p.L ? p.ef_slide : p.L;
-    const bool cm = (p.flags & RNSM_FLAG_CM) != 0;
-    std::vector<int64_t> h_offs;
-    std::vector<int32_t> h_ids;
-    int32_t lists_for = -1;  // source segment whose pivot lists are in the device buffers
 
-    for (const PlanEdge &e : pl) {
-        const rnsm_segment &S = segs[e.src], &T = segs[e.dst];
-        const int64_t ns = S.n, nt = T.n;
-        const int32_t s0 = (int32_t)tab.off[e.src], t0 = (int32_t)tab.off[e.dst];
-        SrcCache &sc = cache[e.src];
-        clk.mark(0, st);
-        clk.mark(1, st);
-        clk.mark(2, st);
-        bool reuse_later = false;
-        for (size_t j = (size_t)(&e - pl.data()) + 1; j < pl.size(); ++j)
-            if (pl[j].src == e.src) reuse_later = true;
-        if (!sc.done) {
-            bool host_lists = true;
-            sc.pivot_of.assign((size_t)ns, -1);
-            sc.pivots.clear();
-            sc.followers.clear();
-            if (cm) {
-                for (int64_t v = 0; v < ns; ++v) sc.pivots.push_back((int32_t)v);
-            } else {
-                // S1: neighbour expansion in the source's own graph.
-                SearchArgs a = search_defaults();
-                a.base = S.vecs;
-                a.n_base = ns;
-                a.adj = S.adj;
-                a.r_in = S.r_in;
-                a.dim = dim;
-                a.metric = p.metric;
-                a.qvecs = S.vecs;
-                a.nq = ns;
-                a.seed_mode = kSeedSelf;
-                a.ef = p.k_plus + 1;
-                a.k = p.k_plus;
-                a.exclude_self = 1;
-                a.out_ids = mb.nplus;
-                a.out_stride = p.k_plus;
-                a.out_by_qidx = 1;
-                a.stats = c.stats;
-                TRY(run_search(a, c.work, st));
-                queries[0] += ns;
-                clk.mark(1, st);
-                // S2: reverse kNN inversion (counting sort by x).
-                CK(launch_rk_pairs(mb.nplus, ns, p.k_plus, p.k_rev, mb.rk_keys, mb.rk_vals,
-                                   c.ecount, st));
-                CK(launch_bucket(mb.rk_keys, mb.rk_vals, ns * p.k_rev, c.ecount, ns, 0, mb.rk_offs,
-                                 mb.rk_cursor, mb.rk_ids, mb.rk_scan, mb.rk_scan_bytes, st));
-                clk.mark(2, st);
-                if (p.flags & RNSM_FLAG_HOST_PIVOTS) {
-                    // S3: lazy greedy on the host.
-                    h_offs.resize((size_t)ns + 1);
-                    h_ids.resize((size_t)(ns * p.k_rev));
-                    CK(cudaMemcpyAsync(h_offs.data(), mb.rk_offs, sizeof(int64_t) * (ns + 1),
-                                       cudaMemcpyDeviceToHost, st));
-                    CK(cudaMemcpyAsync(h_ids.data(), mb.rk_ids, sizeof(int32_t) * ns * p.k_rev,
-                                       cudaMemcpyDeviceToHost, st));
-                    CK(cudaStreamSynchronize(st));
-                    const auto h0 = std::chrono::steady_clock::now();
-                    select_pivots_host(ns, h_offs.data(), h_ids.data(), sc.pivot_of.data(),
-                                       sc.pivots);
-                    for (int64_t y = 0; y < ns; ++y)
-                        if (sc.pivot_of[y] >= 0) sc.followers.push_back((int32_t)y);
-                    host_s += std::chrono::duration<double>(std::chrono::steady_clock::now() - h0)
-                                  .count();
-                } else {
-                    // S3: the same selection in parallel rounds on the device.
-                    int64_t np_ = 0, nf_ = 0;
-                    CK(select_pivots_device(mb.nplus, ns, p.k_plus, p.k_rev, mb.rk_offs, mb.rk_ids,
-                                            mb.pivot_of, mb.pivots, mb.followers, &np_, &nf_,
-                                            nullptr, mb.piv_tmp, c.stats + 6, st));
-                    sc.np = np_;
-                    sc.nf = nf_;
-                    host_lists = false;
-                    lists_for = e.src;
-                    if (reuse_later) {  // keep a host copy: the device lists get overwritten
-                        sc.pivot_of.resize((size_t)ns);
-                        sc.pivots.resize((size_t)np_);
-                        sc.followers.resize((size_t)nf_);
-                        CK(cudaMemcpyAsync(sc.pivot_of.data(), mb.pivot_of, sizeof(int32_t) * ns,
-                                           cudaMemcpyDeviceToHost, st));
-                        if (np_) CK(cudaMemcpyAsync(sc.pivots.data(), mb.pivots,
-                                                    sizeof(int32_t) * np_, cudaMemcpyDeviceToHost, st));
-                        if (nf_) CK(cudaMemcpyAsync(sc.followers.data(), mb.followers,
-                                                    sizeof(int32_t) * nf_, cudaMemcpyDeviceToHost, st));
-                        CK(cudaStreamSynchronize(st));
-                    }
-                }
-            }
-            if (host_lists) {
-                sc.np = (int64_t)sc.pivots.size();
-                sc.nf = (int64_t)sc.followers.size();
-                lists_for = -1;
-            }
-            sc.done = true;
-        }
-        const int64_t np = sc.np, nf = sc.nf;
-        n_piv += np;
-        n_fol += nf;
-        if (lists_for != e.src) {
-            if (np) CK(cudaMemcpyAsync(mb.pivots, sc.pivots.data(), sizeof(int32_t) * np,
-                                       cudaMemcpyHostToDevice, st));
-            if (nf) CK(cudaMemcpyAsync(mb.followers, sc.followers.data(), sizeof(int32_t) * nf,
-                                       cudaMemcpyHostToDevice, st));
-            CK(cudaMemcpyAsync(mb.pivot_of, sc.pivot_of.data(), sizeof(int32_t) * ns,
+    if (cm) {
+        // CM: every source vertex is a pivot (naive search), no followers
+        for (int32_t s : srcs) {
+            std::vector<int32_t> iota((size_t)segs[s].n);
+            for (int64_t v = 0; v < segs[s].n; ++v) iota[(size_t)v] = (int32_t)v;
+            CK(cudaMemcpyAsync(mb.pivots + tab.off[s], iota.data(), sizeof(int32_t) * iota.size(),
                                cudaMemcpyHostToDevice, st));
-            lists_for = e.src;
+            CK(cudaStreamSynchronize(st));
+            np[(size_t)s] = segs[s].n;
         }
-        clk.mark(3, st);
-        // S4: naive search of the pivots from the target's default entry.
+    } else if (!srcs.empty()) {
+        // S1: neighbour expansion of every source in its own graph, one launch
+        const int t1 = tm.begin(1);
+        std::vector<SearchJob> jobs;
+        int64_t total = 0;
+        for (int32_t s : srcs) {
+            jobs.push_back(make_job(segs[s], segs[s].vecs, nullptr,
+                                    mb.nplus + tab.off[s] * p.k_plus, total));
+            total += segs[s].n;
+        }
+        TRY(upload_jobs(jobs, total, mb.jobs1, st));
+        SearchArgs a = search_defaults();
+        a.dim = dim;
+        a.metric = p.metric;
+        a.nq = total;
+        a.seed_mode = kSeedSelf;
+        a.ef = p.k_plus + 1;
+        a.k = p.k_plus;
+        a.exclude_self = 1;
+        a.out_stride = p.k_plus;
+        a.out_by_qidx = 1;
+        a.stats = c.stats;
+        a.jobs = mb.jobs1;
+        a.n_jobs = (int32_t)srcs.size();
+        TRY(run_search(a, c.work, st));
+        queries[0] += total;
+        tm.end(t1);
+        // S2 (reverse kNN inversion) and S3 (pivots) per source
+        for (int32_t s : srcs) {
+            const int64_t ns = segs[s].n;
+            const int32_t *nplus = mb.nplus + tab.off[s] * p.k_plus;
+            int32_t *pivot_of = mb.pivot_of + tab.off[s];
+            int32_t *pivots = mb.pivots + tab.off[s];
+            int32_t *followers = mb.followers + tab.off[s];
+            const int t2 = tm.begin(2);
+            CK(launch_rk_pairs(nplus, ns, p.k_plus, p.k_rev, mb.rk_keys, mb.rk_vals, c.ecount, st));
+            CK(launch_bucket(mb.rk_keys, mb.rk_vals, ns * p.k_rev, c.ecount, ns, 0, mb.rk_offs,
+                             mb.rk_cursor, mb.rk_ids, mb.rk_scan, mb.rk_scan_bytes, st));
+            tm.end(t2);
+            const int t3 = tm.begin(3);
+            if (p.flags & RNSM_FLAG_HOST_PIVOTS) {
+                // S3: lazy greedy on the host
+                std::vector<int64_t> h_offs((size_t)ns + 1);
+                std::vector<int32_t> h_ids((size_t)(ns * p.k_rev)), h_pof((size_t)ns, -1), h_piv, h_fol;
+                CK(cudaMemcpyAsync(h_offs.data(), mb.rk_offs, sizeof(int64_t) * (ns + 1),
+                                   cudaMemcpyDeviceToHost, st));
+                CK(cudaMemcpyAsync(h_ids.data(), mb.rk_ids, sizeof(int32_t) * ns * p.k_rev,
+                                   cudaMemcpyDeviceToHost, st));
+                CK(cudaStreamSynchronize(st));
+                const auto h0 = std::chrono::steady_clock::now();
+                select_pivots_host(ns, h_offs.data(), h_ids.data(), h_pof.data(), h_piv);
+                for (int64_t y = 0; y < ns; ++y)
+                    if (h_pof[(size_t)y] >= 0) h_fol.push_back((int32_t)y);
+                host_s += std::chrono::duration<double>(std::chrono::steady_clock::now() - h0).count();
+                np[(size_t)s] = (int64_t)h_piv.size();
+                nf[(size_t)s] = (int64_t)h_fol.size();
+                if (!h_piv.empty())
+                    CK(cudaMemcpyAsync(pivots, h_piv.data(), sizeof(int32_t) * h_piv.size(),
+                                       cudaMemcpyHostToDevice, st));
+                if (!h_fol.empty())
+                    CK(cudaMemcpyAsync(followers, h_fol.data(), sizeof(int32_t) * h_fol.size(),
+                                       cudaMemcpyHostToDevice, st));
+                CK(cudaMemcpyAsync(pivot_of, h_pof.data(), sizeof(int32_t) * ns,
+                                   cudaMemcpyHostToDevice, st));
+                CK(cudaStreamSynchronize(st));
+            } else {
+                // S3: the same selection in parallel rounds on the device
+                int64_t np_ = 0, nf_ = 0;
+                CK(select_pivots_device(nplus, ns, p.k_plus, p.k_rev, mb.rk_offs, mb.rk_ids,
+                                        pivot_of, pivots, followers, &np_, &nf_, nullptr,
+                                        mb.piv_tmp, c.stats + 6, st));
+                np[(size_t)s] = np_;
+                nf[(size_t)s] = nf_;
+            }
+            tm.end(t3);
+        }
+    }
+
+    // S4 .. S7 over groups of consecutive plan edges
+    const int64_t budget = (int64_t)(kResBudgetBytes / ((size_t)p.L * sizeof(int32_t)));
+    size_t g0 = 0;
+    while (g0 < pl.size()) {
+        size_t g1 = g0;
+        int64_t rows = 0;
+        std::vector<int64_t> res_off;
+        while (g1 < pl.size() && (g1 == g0 || rows + segs[pl[g1].src].n <= budget)) {
+            res_off.push_back(rows);
+            rows += segs[pl[g1].src].n;
+            ++g1;
+        }
+        // S4: naive search of the pivots of every edge of the group, one launch
         {
+            const int t4 = tm.begin(4);
+            std::vector<SearchJob> jobs;
+            int64_t total = 0;
+            for (size_t e = g0; e < g1; ++e) {
+                const int32_t sv = pl[e].src;
+                jobs.push_back(make_job(segs[pl[e].dst], segs[sv].vecs, mb.pivots + tab.off[sv],
+                                        mb.res + res_off[e - g0] * p.L, total));
+                total += np[(size_t)sv];
+                n_piv += np[(size_t)sv];
+            }
+            TRY(upload_jobs(jobs, total, mb.jobs4, st));
             SearchArgs a = search_defaults();
-            a.base = T.vecs;
-            a.n_base = nt;
-            a.adj = T.adj;
-            a.r_in = T.r_in;
             a.dim = dim;
             a.metric = p.metric;
-            a.qvecs = S.vecs;
-            a.qidx = mb.pivots;
-            a.nq = np;
+            a.nq = total;
             a.seed_mode = kSeedConst;
-            a.seed_const = T.entry;
             a.ef = p.L;
             a.k = p.L;
-            a.out_ids = mb.res;
             a.out_stride = p.L;
             a.out_by_qidx = 1;
             a.stats = c.stats + 2;
+            a.jobs = mb.jobs4;
+            a.n_jobs = (int32_t)(g1 - g0);
             TRY(run_search(a, c.work, st));
-            queries[1] += np;
+            queries[1] += total;
+            tm.end(t4);
         }
-        clk.mark(4, st);
-        // S5: local sliding of the followers from their pivot's results.
-        if (nf) {
-            SearchArgs a = search_defaults();
-            a.base = T.vecs;
-            a.n_base = nt;
-            a.adj = T.adj;
-            a.r_in = T.r_in;
-            a.dim = dim;
-            a.metric = p.metric;
-            a.qvecs = S.vecs;
-            a.qidx = mb.followers;
-            a.nq = nf;
-            a.seed_mode = kSeedTable;
-            a.seed_tab = mb.res;
-            a.seed_stride = p.L;
-            a.n_seeds = ks;
-            a.seed_row = mb.pivot_of;
-            a.ef = p.ef_slide;
-            a.k = p.ef_slide;
-            a.out_ids = mb.res;
-            a.out_stride = p.L;
-            a.out_by_qidx = 1;
-            a.stats = c.stats + 4;
-            TRY(run_search(a, c.work + 3, st));
-            queries[2] += nf;
-        }
-        clk.mark(5, st);
-        // S6: source-side UpdateGraph: list(v) + first c_cross results -> prune.
-        CK(cudaMemsetAsync(c.ecount, 0, sizeof(unsigned long long), st));
+        // S5: local sliding of the followers of every edge, one launch
         {
-            PruneArgs q = prune_defaults();
-            q.segs = tab;
-            q.dim = dim;
-            q.metric = p.metric;
-            q.alpha = p.alpha;
-            q.R = p.R;
-            q.n_owners = ns;
-            q.owner_base = s0;
-            q.listA = out_adj;
-            q.lenA = p.R;
-            q.listB = mb.res;
-            q.strideB = p.L;
-            q.lenB = p.c_cross;
-            q.offB = t0;
-            q.out = out_adj;
-            q.emit_lo = t0;
-            q.emit_hi = t0 + (int32_t)nt;
-            q.eu = mb.eu;
-            q.ev = mb.ev;
-            q.ecount = c.ecount;
-            q.err = c.err;
-            apply_quant(q, &mb.qb, c.rechecks);
-            TRY(run_prune(q, c.work + 8, c, st));
+            const int t5 = tm.begin(5);
+            std::vector<SearchJob> jobs;
+            int64_t total = 0;
+            for (size_t e = g0; e < g1; ++e) {
+                const int32_t sv = pl[e].src;
+                int32_t *res = mb.res + res_off[e - g0] * p.L;
+                SearchJob j = make_job(segs[pl[e].dst], segs[sv].vecs, mb.followers + tab.off[sv],
+                                       res, total);
+                j.seed_tab = res;
+                j.seed_row = mb.pivot_of + tab.off[sv];
+                jobs.push_back(j);
+                total += nf[(size_t)sv];
+                n_fol += nf[(size_t)sv];
+            }
+            if (total > 0) {
+                TRY(upload_jobs(jobs, total, mb.jobs5, st));
+                SearchArgs a = search_defaults();
+                a.dim = dim;
+                a.metric = p.metric;
+                a.nq = total;
+                a.seed_mode = kSeedTable;
+                a.seed_stride = p.L;
+                a.n_seeds = ks;
+                a.ef = p.ef_slide;
+                a.k = p.ef_slide;
+                a.out_stride = p.L;
+                a.out_by_qidx = 1;
+                a.stats = c.stats + 4;
+                a.jobs = mb.jobs5;
+                a.n_jobs = (int32_t)(g1 - g0);
+                TRY(run_search(a, c.work + 3, st));
+                queries[2] += total;
+            }
+            tm.end(t5);
         }
-        clk.mark(6, st);
-        // S7: reverse edges into the target (counting sort by u, then prune).
-        TRY(reverse_into(tab, dim, p, out_adj, mb.eu, mb.ev, ns * p.R, c.ecount, t0, nt, -1,
-                         mb.rev, c, st, &mb.qb));
-        clk.mark(7, st);
-        unsigned long long ne = 0;
-        CK(cudaMemcpyAsync(&ne, c.ecount, sizeof(ne), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        clk.add(phase_ms, 0, 7, 1);  // marks 0..7 bound S1..S7
-        rev_total += ne;
+        // S6 and S7 per edge, in plan order
+        for (size_t e = g0; e < g1; ++e) {
+            const PlanEdge &E = pl[e];
+            const int64_t ns = segs[E.src].n, nt = segs[E.dst].n;
+            const int32_t s0 = (int32_t)tab.off[E.src], t0 = (int32_t)tab.off[E.dst];
+            const int t6 = tm.begin(6);
+            CK(cudaMemsetAsync(c.ecount, 0, sizeof(unsigned long long), st));
+            {
+                PruneArgs q = prune_defaults();
+                q.segs = tab;
+                q.dim = dim;
+                q.metric = p.metric;
+                q.alpha = p.alpha;
+                q.R = p.R;
+                q.n_owners = ns;
+                q.owner_base = s0;
+                q.listA = out_adj;
+                q.lenA = p.R;
+                q.listB = mb.res + res_off[e - g0] * p.L;
+                q.strideB = p.L;
+                q.lenB = p.c_cross;
+                q.offB = t0;
+                q.out = out_adj;
+                q.emit_lo = t0;
+                q.emit_hi = t0 + (int32_t)nt;
+                q.eu = mb.eu;
+                q.ev = mb.ev;
+                q.ecount = c.ecount;
+                q.err = c.err;
+                apply_quant(q, &mb.qb, c.rechecks, c.tile_err);
+                TRY(run_prune(q, c.work + 8, c, st));
+            }
+            tm.end(t6);
+            const int t7 = tm.begin(7);
+            TRY(reverse_into(tab, dim, p, out_adj, mb.eu, mb.ev, ns * p.R, c.ecount, t0, nt, -1,
+                             mb.rev, c, st, &mb.qb));
+            tm.end(t7);
+            unsigned long long ne = 0;
+            CK(cudaMemcpyAsync(&ne, c.ecount, sizeof(ne), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            rev_total += ne;
+        }
+        g0 = g1;
     }
     TRY(check_err_word(c, st));
     if (stats) {
         unsigned long long hs[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         CK(cudaMemcpyAsync(hs, c.stats, sizeof(hs), cudaMemcpyDeviceToHost, st));
+        unsigned long long rc = 0;
+        unsigned int te[4] = {0, 0, 0, 0};
+        CK(cudaMemcpyAsync(&rc, c.rechecks, sizeof(rc), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(te, c.tile_err, sizeof(te), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
+        for (int i = 0; i < 3; ++i) {
+            float f;
+            std::memcpy(&f, &te[i], sizeof(f));
+            stats->tile_error[i] = f;
+        }
+        stats->tile_error[3] = te[3];
         stats->ndc = (int64_t)(hs[0] + hs[2] + hs[4]);
         stats->expansions = (int64_t)(hs[1] + hs[3] + hs[5]);
         for (int i = 0; i < 3; ++i) {
@@ -1104,15 +1211,13 @@ rnsm_status rnsm_merge(const rnsm_segment *segs, int32_t m, const rnsm_params *p
             stats->search_queries[i] = queries[i];
         }
         stats->launches = launches_so_far() - launches0;
-        unsigned long long rc = 0;
-        CK(cudaMemcpyAsync(&rc, c.rechecks, sizeof(rc), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
         stats->rechecks = (int64_t)rc;
         stats->near_ties = 0;
         stats->pivots = n_piv;
         stats->followers = n_fol;
         stats->reverse_edges = (int64_t)rev_total;
         stats->host_pivot_s = host_s;
+        tm.add(phase_ms);
         stats->wall_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         for (int i = 0; i < 8; ++i) stats->phase_ms[i] = phase_ms[i];
     }

@@ -17,9 +17,30 @@ long long launches_so_far();
 
 enum SeedMode : int32_t { kSeedConst = 0, kSeedSelf = 1, kSeedTable = 2 };
 
+// One (source, target) pair of a multi-job search launch: its fields replace
+// those of the same names in SearchArgs for the queries
+// [q_begin, next job's q_begin) of the launch.
+struct SearchJob {
+    const float *base;
+    const int32_t *adj;
+    const float *qvecs;
+    const int32_t *qidx;
+    const int32_t *seed_tab;
+    const int32_t *seed_row;
+    int32_t *out_ids;
+    int64_t q_begin;
+    int64_t n_base;
+    int32_t r_in;
+    int32_t seed_const;
+    int32_t id_offset;
+    int32_t pad;
+};
+
 // One batched beam-search launch (Algorithm 1).  Query i of the launch is
 // query g = q0 + i of the batch; it reads qvecs[qrow * dim] with
-// qrow = qidx ? qidx[g] : g.
+// qrow = qidx ? qidx[g] : g.  With a job table (jobs, device memory,
+// n_jobs + 1 entries, the last one a sentinel whose q_begin is the total),
+// g selects the job and counts from the job's q_begin; nq is the total.
 struct SearchArgs {
     const float *base;      // searched vector set [n_base * dim]
     int64_t n_base;
@@ -48,9 +69,12 @@ struct SearchArgs {
     int64_t *out_ndc;         // nullable, [nq]
     unsigned long long *stats;  // nullable: [0] += NDC, [1] += expansions
     int32_t *work;            // zeroed work counter
+    const SearchJob *jobs;    // nullable: multi-job launch (out_d and out_ndc unused)
+    int32_t n_jobs;
 };
 
 cudaError_t launch_search(const SearchArgs &a, cudaStream_t st);
+cudaError_t launch_search_jobs(const SearchArgs &a, int var, cudaStream_t st);
 // Launch-shape variant the search autotuner chose for (dim, ef), -1 if none yet.
 int search_variant_for(int dim, int ef);
 
@@ -90,17 +114,23 @@ struct PruneArgs {
     const float *qerr;        // residual norms ||x - x~||
     const float *qnorm;       // row norms ||x||
     unsigned long long *rechecks;  // decisions re-decided in FP32
+    unsigned int *tile_err;   // nullable [4]: sampled tile error maxima (float bits) and count
     int32_t *work;
     int32_t *work2;           // second zeroed counter (overflow pass)
     int32_t *ovf_list;        // [n_owners]: owners whose pool exceeds the small-pool kernel
     unsigned long long *ovf_count;
-    int32_t *err;             // bit 4: pool larger than the capacity
+    int32_t *err;             // bit 4: pool larger than the capacity; bit 6: tile wait ran out
+    int32_t test_withhold_commit;  // test-only (tensor-core prune): never signal MMA completion
 };
 
 cudaError_t launch_prune(const PruneArgs &a, cudaStream_t st);
 
-// Tensor-core small-pool prune (BF16 / FP8 tiles with FP32 re-decisions).
-bool prune_tc_supported(int dim, int prec);
+// Tensor-core prune (BF16 / FP8 tiles with FP32 re-decisions) of pools up to
+// prune_tc_max_pool() raw candidates.  prune_tc_terms: 0 if (dim, prec) has no
+// tensor-core tile, 1 if it stages the quantized rows (qrows, qscale, qerr,
+// qnorm), 2 if it stages the FP32 rows split into two BF16 terms.
+int prune_tc_terms(int dim, int prec);
+int prune_tc_max_pool();
 cudaError_t launch_prune_tc(const PruneArgs &a, cudaStream_t st);
 // Rows of the segment table to BF16 (prec 1) or E4M3 with per-row scale (prec 2),
 // plus residual norms and row norms.

@@ -761,18 +761,17 @@ cudaError_t launch_small(const PruneArgs &a, cudaStream_t st);
 cudaError_t launch_prune(const PruneArgs &a, cudaStream_t st) {
     if (a.n_owners <= 0) return cudaSuccess;
     if (a.R > 64 || a.dim > 1024 || (a.dim & 3)) return cudaErrorInvalidValue;
-    const bool small_ok = a.ovf_list && a.ovf_count && a.work2 && a.lenA + a.lenB <= kSmallMax;
+    const int terms = a.prec != 0 ? prune_tc_terms(a.dim, a.prec) : 0;
+    const bool tc = terms == 2 || (terms == 1 && a.qrows);
+    const int cap = tc ? prune_tc_max_pool() : kSmallMax;   // pool of the first kernel
+    const bool small_ok = a.ovf_list && a.ovf_count && a.work2 && a.lenA + a.lenB <= cap;
     if (!small_ok) return launch_general(a, nullptr, nullptr, st);
     cudaError_t e = cudaMemsetAsync(a.ovf_count, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
-    if (a.prec != 0 && a.qrows && prune_tc_supported(a.dim, a.prec)) {
-        e = launch_prune_tc(a, st);
-    } else {
-        e = launch_small(a, st);
-    }
+    e = tc ? launch_prune_tc(a, st) : launch_small(a, st);
     if (e != cudaSuccess) return e;
-    if (a.lenA + a.lenB + (a.csr_offs ? a.csr_max : 0) <= kSmallMax) return cudaSuccess;
-    // owners whose pools exceeded 64 raw candidates (the count stays on the device)
+    if (a.lenA + a.lenB + (a.csr_offs ? a.csr_max : 0) <= cap) return cudaSuccess;
+    // owners whose pools exceeded the first kernel (the count stays on the device)
     PruneArgs b = a;
     b.work = a.work2;
     e = cudaMemsetAsync(b.work, 0, sizeof(int32_t), st);

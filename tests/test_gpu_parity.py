@@ -246,6 +246,24 @@ def test_merge_multi_segment_plan_exact(rn):
     np.testing.assert_array_equal(got, want)
 
 
+@pytest.mark.parametrize("flags", [0, 2])
+def test_merge_batched_plan_with_shared_sources_exact(rn, flags):
+    # six uneven segments, a hand-made plan where sources serve several edges and
+    # segments are source and target in turn: the batched executor (all S1 in
+    # one launch, all S4 and all S5 of the plan in one launch each) must give
+    # Algorithm 2 applied edge by edge
+    sizes = [700, 1300, 450, 1000, 820, 1600]
+    segs = [gen.sift_like(n, 60 + i, d=64) for i, n in enumerate(sizes)]
+    gs = [oracle.build_graph(s, 16, 32, 1.2) for s in segs]
+    plan = [(2, 0), (2, 1), (0, 1), (4, 3), (1, 5), (3, 5), (2, 4), (0, 3), (4, 5)]
+    want, wst = oracle.rnsm_merge(segs, [g for g, _ in gs], [e for _, e in gs], plan, 16, 32, 1.2)
+    tsegs = [(dev(sg), dev(g), e) for sg, (g, e) in zip(segs, gs)]
+    got, gst = rn.merge(tsegs, rn.params(16, 32, 1.2, flags=flags), [(a, b, 0.0) for a, b in plan])
+    np.testing.assert_array_equal(host(got), want)
+    assert gst["reverse_edges"] == wst["reverse_edges"]
+    assert gst["pivots"] == wst["pivots"] and gst["followers"] == wst["followers"]
+
+
 def test_merge_float_data_recall_within_tolerance(rn):
     segs, Q = gen.tiny_case()
     gs = [oracle.build_graph(s, 16, 32, 1.2) for s in segs]
@@ -335,9 +353,16 @@ def test_merge_host_and_device_pivots_agree(rn):
 # ------------------------------------------- precision pattern (BF16 / FP8)
 
 @pytest.mark.parametrize("prec", [1, 2])
-@pytest.mark.parametrize("kind,d,w", [("gauss", 32, 64), ("gauss", 128, 48), ("deep", 96, 64),
-                                      ("sift", 128, 64), ("embed", 256, 40), ("gauss", 128, 100)])
-def test_low_precision_prune_equals_fp32(rn, prec, kind, d, w):
+@pytest.mark.parametrize("kind,d,w,R", [
+    ("gauss", 32, 64, 32), ("gauss", 128, 48, 32), ("deep", 96, 64, 32), ("sift", 128, 64, 32),
+    ("embed", 256, 40, 32), ("gauss", 128, 100, 32),
+    # pools of up to 128 raw candidates, K-chunked rows, the split BF16 tile (d >= 384)
+    ("deep", 96, 128, 64), ("sift", 128, 120, 64), ("embed", 768, 128, 64),
+    ("gauss", 512, 128, 64), ("embed", 384, 96, 48), ("gauss", 1024, 70, 32),
+    ("sift", 160, 128, 16),
+    # pools above 128 overflow to the FP32 general kernel
+    ("embed", 768, 150, 64)])
+def test_low_precision_prune_equals_fp32(rn, prec, kind, d, w, R):
     n = 3000
     X = {"gauss": lambda: gen.gaussian(n, d, 90),
          "deep": lambda: gen.deep_like(n, 91, d=d),
@@ -346,11 +371,11 @@ def test_low_precision_prune_equals_fp32(rn, prec, kind, d, w):
     metric = oracle.IP if kind in ("deep", "embed") else oracle.L2
     owners, pool = _pools(n, w, 7 * d + w, 800)
     Xd, od, pd_ = dev(X), dev(owners), dev(pool)
-    want = rn.prune(Xd, od, pd_, 32, 1.2, metric=metric)
-    got = rn.prune(Xd, od, pd_, 32, 1.2, metric=metric, prec=prec)
+    want = rn.prune(Xd, od, pd_, R, 1.2, metric=metric)
+    got = rn.prune(Xd, od, pd_, R, 1.2, metric=metric, prec=prec)
     np.testing.assert_array_equal(host(got), host(want))
-    want2 = rn.prune(Xd, od, pd_, 32, 1.2, metric=metric, keep_all_if_fit=True)
-    got2 = rn.prune(Xd, od, pd_, 32, 1.2, metric=metric, keep_all_if_fit=True, prec=prec)
+    want2 = rn.prune(Xd, od, pd_, R, 1.2, metric=metric, keep_all_if_fit=True)
+    got2 = rn.prune(Xd, od, pd_, R, 1.2, metric=metric, keep_all_if_fit=True, prec=prec)
     np.testing.assert_array_equal(host(got2), host(want2))
 
 
@@ -368,8 +393,26 @@ def test_low_precision_merge_equals_fp32(rn, prec):
         b, sb = rn.merge(tsegs, rn.params(R, L, 1.2, metric=metric, prec=prec))
         np.testing.assert_array_equal(host(b), host(a))
         assert sa["rechecks"] == 0
+        # sampled tile distances stay inside their error bounds
+        assert sb["tile_error"][3] > 0 and sb["tile_error"][2] <= 1.0
+        assert sa["tile_error"][3] == 0
         if segs[0].dtype == np.float32 and not (segs[0] == np.rint(segs[0])).all():
             assert sb["rechecks"] > 0       # real-valued data: some decisions re-decided
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_low_precision_merge_equals_fp32_embedding_shape(rn, prec):
+    # d = 768, inner product, R = 64, L = 128: source pools of R + c_cross = 128
+    # candidates go to the tensor-core tile (the split BF16 tile for prec 1)
+    X = gen.embed_like(4000, 99, d=768, n_comp=40)
+    segs = [X[:2200], X[2200:]]
+    gs = [oracle.build_graph(s, 64, 128, 1.2, metric=oracle.IP) for s in segs]
+    tsegs = [(dev(s), dev(g), e) for s, (g, e) in zip(segs, gs)]
+    a, _ = rn.merge(tsegs, rn.params(64, 128, 1.2, metric=oracle.IP))
+    b, sb = rn.merge(tsegs, rn.params(64, 128, 1.2, metric=oracle.IP, prec=prec))
+    np.testing.assert_array_equal(host(b), host(a))
+    assert sb["rechecks"] > 0
+    assert sb["tile_error"][3] > 0 and sb["tile_error"][2] <= 1.0
 
 
 # ---------------------------------------------------------------- autotuner
