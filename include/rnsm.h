@@ -99,6 +99,12 @@ typedef struct {
 /* Run pivot selection (S3) with the host lazy greedy instead of the device
  * rounds (identical results; for cross-checking). */
 #define RNSM_FLAG_HOST_PIVOTS 0x2u
+/* Capture the searches, prunes and reverse-edge updates of the plan (S4 to S7)
+ * in a CUDA graph and replay it when the next call has the same inputs,
+ * parameters, plan and pivot counts (identical results; the capture is used
+ * once the search launch shapes are autotuned and the plan's result tables
+ * fit one group).  phase_ms[4] then holds S4 to S7 together. */
+#define RNSM_FLAG_GRAPH 0x4u
 
 /* One edge of a merge plan: segment `src` is merged into segment `dst`.
  * Plan order = array order (Section 5: closer pairs first). */

@@ -52,6 +52,26 @@ struct DevWs {
     size_t size = 0;
 } g_ws[kMaxDev];
 
+// The captured S4..S7 sequence of the last graph-mode call on a device.
+struct GraphCache {
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t stream = nullptr;   // capture stream (kept for the process)
+    std::string key;
+    long long launches = 0;
+    void reset() {
+        if (exec) cudaGraphExecDestroy(exec);
+        exec = nullptr;
+        key.clear();
+    }
+};
+GraphCache g_graphs[kMaxDev];
+
+int cur_device() {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    return dev >= 0 && dev < kMaxDev ? dev : 0;
+}
+
 // Bump allocator over the device workspace (256-byte aligned slices).
 struct Bump {
     char *base = nullptr;
@@ -330,6 +350,7 @@ const char *rnsm_version(void) { return "rnsm-gb300 0.1 (sm_103a)"; }
 
 void rnsm_release_workspace(void) {
     std::lock_guard<std::mutex> lk(g_mu);
+    g_graphs[cur_device()].reset();   // captured launches point into the workspace
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return;
     if (g_ws[dev].ptr) {
@@ -770,6 +791,7 @@ struct MergeBufs {
     int32_t *res;                          // [res_rows * L]
     int32_t *eu, *ev;
     SearchJob *jobs1, *jobs4, *jobs5;
+    unsigned long long *rev_counts;        // [plan edges] kept cross edges per edge
     RevBufs rev;
     QuantBufs qb;
 };
@@ -795,6 +817,7 @@ void carve_merge(Bump &b, const rnsm_params &p, int64_t nmax, int64_t n_all, int
     m.jobs1 = b.take<SearchJob>(n_jobs + 1);
     m.jobs4 = b.take<SearchJob>(n_jobs + 1);
     m.jobs5 = b.take<SearchJob>(n_jobs + 1);
+    m.rev_counts = b.take<unsigned long long>(n_jobs + 1);
     take_rev(b, nmax, nmax * p.R, m.rev);
     take_quant(b, n_all, dim, qprec, m.qb);
 }
@@ -891,6 +914,40 @@ rnsm_status resolve_plan(const rnsm_segment *segs, int32_t m, const mos_edge *pl
         return fail(RNSM_EINVAL, "m > 2 needs a plan (mos_plan)");
     }
     return RNSM_OK;
+}
+
+// Largest reverse-edge pool a prune accepts (list + incoming); pools above it set
+// error bit 16.  Captured launches size the overflow prune for it.
+constexpr int32_t kReversePoolBound = 4096;
+
+// Everything the captured launches depend on.
+std::string graph_key(const rnsm_segment *segs, int32_t m, const rnsm_params &p,
+                      const std::vector<PlanEdge> &pl, const int32_t *out_adj, const char *ws,
+                      const std::vector<int64_t> &np, const std::vector<int64_t> &nf, int32_t dim,
+                      int32_t qprec) {
+    std::string k;
+    auto put = [&k](const auto &v) { k.append(reinterpret_cast<const char *>(&v), sizeof(v)); };
+    put(m);
+    put(dim);
+    put(qprec);
+    put(p);
+    put(out_adj);
+    put(ws);
+    for (int32_t s = 0; s < m; ++s) {
+        put(segs[s].n);
+        put(segs[s].dim);
+        put(segs[s].r_in);
+        put(segs[s].vecs);
+        put(segs[s].adj);
+        put(segs[s].entry);
+        put(np[(size_t)s]);
+        put(nf[(size_t)s]);
+    }
+    for (const PlanEdge &e : pl) {
+        put(e.src);
+        put(e.dst);
+    }
+    return k;
 }
 
 }  // namespace
@@ -1068,33 +1125,48 @@ rnsm_status rnsm_merge(const rnsm_segment *segs, int32_t m, const rnsm_params *p
 
     // S4 .. S7 over groups of consecutive plan edges
     const int64_t budget = (int64_t)(kResBudgetBytes / ((size_t)p.L * sizeof(int32_t)));
-    size_t g0 = 0;
-    while (g0 < pl.size()) {
+    std::vector<std::pair<size_t, size_t>> groups;
+    std::vector<int64_t> res_off(pl.size(), 0);
+    for (size_t g0 = 0; g0 < pl.size();) {
         size_t g1 = g0;
         int64_t rows = 0;
-        std::vector<int64_t> res_off;
         while (g1 < pl.size() && (g1 == g0 || rows + segs[pl[g1].src].n <= budget)) {
-            res_off.push_back(rows);
+            res_off[g1] = rows;
             rows += segs[pl[g1].src].n;
             ++g1;
         }
-        // S4: naive search of the pivots of every edge of the group, one launch
-        {
-            const int t4 = tm.begin(4);
-            std::vector<SearchJob> jobs;
-            int64_t total = 0;
-            for (size_t e = g0; e < g1; ++e) {
-                const int32_t sv = pl[e].src;
-                jobs.push_back(make_job(segs[pl[e].dst], segs[sv].vecs, mb.pivots + tab.off[sv],
-                                        mb.res + res_off[e - g0] * p.L, total));
-                total += np[(size_t)sv];
-                n_piv += np[(size_t)sv];
+        groups.push_back({g0, g1});
+        g0 = g1;
+    }
+    // the job tables of a group (host side; uploaded before its launches)
+    auto jobs_of = [&](size_t g0, size_t g1, bool followers, int64_t &total) {
+        std::vector<SearchJob> jobs;
+        total = 0;
+        for (size_t e = g0; e < g1; ++e) {
+            const int32_t sv = pl[e].src;
+            int32_t *res = mb.res + res_off[e] * p.L;
+            SearchJob j = make_job(segs[pl[e].dst], segs[sv].vecs,
+                                   (followers ? mb.followers : mb.pivots) + tab.off[sv], res, total);
+            if (followers) {
+                j.seed_tab = res;
+                j.seed_row = mb.pivot_of + tab.off[sv];
             }
-            TRY(upload_jobs(jobs, total, mb.jobs4, st));
+            jobs.push_back(j);
+            total += followers ? nf[(size_t)sv] : np[(size_t)sv];
+        }
+        return jobs;
+    };
+    // enqueues S4, S5 and the per-edge S6 / S7 of a group; no host synchronisation
+    // when `graph` (the reverse pools are then sized by their static bound)
+    auto enqueue_group = [&](size_t gi, bool graph, int64_t tot4, int64_t tot5,
+                             cudaStream_t es) -> rnsm_status {
+        const size_t g0 = groups[gi].first, g1 = groups[gi].second;
+        int span = graph ? -1 : tm.begin(4);
+        {   // S4: naive search of the pivots of every edge of the group, one launch
             SearchArgs a = search_defaults();
             a.dim = dim;
             a.metric = p.metric;
-            a.nq = total;
+            a.nq = tot4;
             a.seed_mode = kSeedConst;
             a.ef = p.L;
             a.k = p.L;
@@ -1103,90 +1175,125 @@ rnsm_status rnsm_merge(const rnsm_segment *segs, int32_t m, const rnsm_params *p
             a.stats = c.stats + 2;
             a.jobs = mb.jobs4;
             a.n_jobs = (int32_t)(g1 - g0);
-            TRY(run_search(a, c.work, st));
-            queries[1] += total;
-            tm.end(t4);
+            TRY(run_search(a, c.work, es));
         }
-        // S5: local sliding of the followers of every edge, one launch
-        {
-            const int t5 = tm.begin(5);
-            std::vector<SearchJob> jobs;
-            int64_t total = 0;
-            for (size_t e = g0; e < g1; ++e) {
-                const int32_t sv = pl[e].src;
-                int32_t *res = mb.res + res_off[e - g0] * p.L;
-                SearchJob j = make_job(segs[pl[e].dst], segs[sv].vecs, mb.followers + tab.off[sv],
-                                       res, total);
-                j.seed_tab = res;
-                j.seed_row = mb.pivot_of + tab.off[sv];
-                jobs.push_back(j);
-                total += nf[(size_t)sv];
-                n_fol += nf[(size_t)sv];
-            }
-            if (total > 0) {
-                TRY(upload_jobs(jobs, total, mb.jobs5, st));
-                SearchArgs a = search_defaults();
-                a.dim = dim;
-                a.metric = p.metric;
-                a.nq = total;
-                a.seed_mode = kSeedTable;
-                a.seed_stride = p.L;
-                a.n_seeds = ks;
-                a.ef = p.ef_slide;
-                a.k = p.ef_slide;
-                a.out_stride = p.L;
-                a.out_by_qidx = 1;
-                a.stats = c.stats + 4;
-                a.jobs = mb.jobs5;
-                a.n_jobs = (int32_t)(g1 - g0);
-                TRY(run_search(a, c.work + 3, st));
-                queries[2] += total;
-            }
-            tm.end(t5);
+        tm.end(span);
+        span = graph ? -1 : tm.begin(5);
+        if (tot5 > 0) {   // S5: local sliding of the followers of every edge, one launch
+            SearchArgs a = search_defaults();
+            a.dim = dim;
+            a.metric = p.metric;
+            a.nq = tot5;
+            a.seed_mode = kSeedTable;
+            a.seed_stride = p.L;
+            a.n_seeds = ks;
+            a.ef = p.ef_slide;
+            a.k = p.ef_slide;
+            a.out_stride = p.L;
+            a.out_by_qidx = 1;
+            a.stats = c.stats + 4;
+            a.jobs = mb.jobs5;
+            a.n_jobs = (int32_t)(g1 - g0);
+            TRY(run_search(a, c.work + 3, es));
         }
-        // S6 and S7 per edge, in plan order
-        for (size_t e = g0; e < g1; ++e) {
+        tm.end(span);
+        for (size_t e = g0; e < g1; ++e) {   // S6 and S7 per edge, in plan order
             const PlanEdge &E = pl[e];
             const int64_t ns = segs[E.src].n, nt = segs[E.dst].n;
             const int32_t s0 = (int32_t)tab.off[E.src], t0 = (int32_t)tab.off[E.dst];
-            const int t6 = tm.begin(6);
-            CK(cudaMemsetAsync(c.ecount, 0, sizeof(unsigned long long), st));
-            {
-                PruneArgs q = prune_defaults();
-                q.segs = tab;
-                q.dim = dim;
-                q.metric = p.metric;
-                q.alpha = p.alpha;
-                q.R = p.R;
-                q.n_owners = ns;
-                q.owner_base = s0;
-                q.listA = out_adj;
-                q.lenA = p.R;
-                q.listB = mb.res + res_off[e - g0] * p.L;
-                q.strideB = p.L;
-                q.lenB = p.c_cross;
-                q.offB = t0;
-                q.out = out_adj;
-                q.emit_lo = t0;
-                q.emit_hi = t0 + (int32_t)nt;
-                q.eu = mb.eu;
-                q.ev = mb.ev;
-                q.ecount = c.ecount;
-                q.err = c.err;
-                apply_quant(q, &mb.qb, c.rechecks, c.tile_err);
-                TRY(run_prune(q, c.work + 8, c, st));
-            }
-            tm.end(t6);
-            const int t7 = tm.begin(7);
-            TRY(reverse_into(tab, dim, p, out_adj, mb.eu, mb.ev, ns * p.R, c.ecount, t0, nt, -1,
-                             mb.rev, c, st, &mb.qb));
-            tm.end(t7);
-            unsigned long long ne = 0;
-            CK(cudaMemcpyAsync(&ne, c.ecount, sizeof(ne), cudaMemcpyDeviceToHost, st));
-            CK(cudaStreamSynchronize(st));
-            rev_total += ne;
+            span = graph ? -1 : tm.begin(6);
+            CK(cudaMemsetAsync(c.ecount, 0, sizeof(unsigned long long), es));
+            PruneArgs q = prune_defaults();
+            q.segs = tab;
+            q.dim = dim;
+            q.metric = p.metric;
+            q.alpha = p.alpha;
+            q.R = p.R;
+            q.n_owners = ns;
+            q.owner_base = s0;
+            q.listA = out_adj;
+            q.lenA = p.R;
+            q.listB = mb.res + res_off[e] * p.L;
+            q.strideB = p.L;
+            q.lenB = p.c_cross;
+            q.offB = t0;
+            q.out = out_adj;
+            q.emit_lo = t0;
+            q.emit_hi = t0 + (int32_t)nt;
+            q.eu = mb.eu;
+            q.ev = mb.ev;
+            q.ecount = c.ecount;
+            q.err = c.err;
+            apply_quant(q, &mb.qb, c.rechecks, c.tile_err);
+            TRY(run_prune(q, c.work + 8, c, es));
+            tm.end(span);
+            span = graph ? -1 : tm.begin(7);
+            TRY(reverse_into(tab, dim, p, out_adj, mb.eu, mb.ev, ns * p.R, c.ecount, t0, nt,
+                             graph ? kReversePoolBound - p.R : -1, mb.rev, c, es, &mb.qb));
+            CK(cudaMemcpyAsync(mb.rev_counts + e, c.ecount, sizeof(unsigned long long),
+                               cudaMemcpyDeviceToDevice, es));
+            tm.end(span);
         }
-        g0 = g1;
+        return RNSM_OK;
+    };
+    for (size_t gi = 0; gi < groups.size(); ++gi) {
+        int64_t tot4 = 0, tot5 = 0;
+        std::vector<SearchJob> j4 = jobs_of(groups[gi].first, groups[gi].second, false, tot4);
+        std::vector<SearchJob> j5 = jobs_of(groups[gi].first, groups[gi].second, true, tot5);
+        // capture only what replays unchanged: one group, no autotuning inside
+        const bool want_graph = (p.flags & RNSM_FLAG_GRAPH) && groups.size() == 1 &&
+                                !search_would_tune(dim, p.L, tot4) &&
+                                !search_would_tune(dim, p.ef_slide, tot5);
+        TRY(upload_jobs(j4, tot4, mb.jobs4, st));
+        TRY(upload_jobs(j5, tot5, mb.jobs5, st));
+        for (size_t e = groups[gi].first; e < groups[gi].second; ++e) {
+            n_piv += np[(size_t)pl[e].src];
+            n_fol += nf[(size_t)pl[e].src];
+        }
+        queries[1] += tot4;
+        queries[2] += tot5;
+        if (!want_graph) {
+            TRY(enqueue_group(gi, false, tot4, tot5, st));
+            continue;
+        }
+        // graph mode: capture once, replay while the key matches
+        std::string key = graph_key(segs, m, p, pl, out_adj, b.base, np, nf, dim, qprec);
+        GraphCache &gc = g_graphs[cur_device()];
+        const bool replay = gc.exec && gc.key == key;
+        if (!replay) {
+            gc.reset();
+            const long long l0 = launches_so_far();
+            // capture on the library's own stream (the legacy default stream cannot be
+            // captured); the graph is launched on the caller's stream below
+            if (!gc.stream) CK(cudaStreamCreateWithFlags(&gc.stream, cudaStreamNonBlocking));
+            CK(cudaStreamBeginCapture(gc.stream, cudaStreamCaptureModeRelaxed));
+            const rnsm_status rs = enqueue_group(gi, true, tot4, tot5, gc.stream);
+            cudaGraph_t graph = nullptr;
+            const cudaError_t ce = cudaStreamEndCapture(gc.stream, &graph);
+            if (rs != RNSM_OK) {
+                if (graph) cudaGraphDestroy(graph);
+                return rs;
+            }
+            CK(ce);
+            const cudaError_t ie = cudaGraphInstantiate(&gc.exec, graph, 0);
+            cudaGraphDestroy(graph);
+            CK(ie);
+            gc.key = key;
+            gc.launches = launches_so_far() - l0;   // kernels one replay launches
+        } else {
+            note_launches((int)gc.launches);
+        }
+        const int span = tm.begin(4);
+        CK(cudaGraphLaunch(gc.exec, st));
+        tm.end(span);
+    }
+    {
+        std::vector<unsigned long long> rc(pl.size(), 0ull);
+        if (!pl.empty())
+            CK(cudaMemcpyAsync(rc.data(), mb.rev_counts, sizeof(unsigned long long) * pl.size(),
+                               cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        for (unsigned long long v : rc) rev_total += v;
     }
     TRY(check_err_word(c, st));
     if (stats) {

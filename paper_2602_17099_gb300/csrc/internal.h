@@ -77,6 +77,8 @@ cudaError_t launch_search(const SearchArgs &a, cudaStream_t st);
 cudaError_t launch_search_jobs(const SearchArgs &a, int var, cudaStream_t st);
 // Launch-shape variant the search autotuner chose for (dim, ef), -1 if none yet.
 int search_variant_for(int dim, int ef);
+// True if a launch of nq queries would run the autotuner (timed slices, host waits).
+bool search_would_tune(int dim, int ef, int64_t nq);
 
 // Occlusion prune (UpdateGraph) of a batch of owners over a segment table.
 // Owner i is global id owner_ids ? owner_ids[i] : owner_base + i.  Its pool

@@ -66,6 +66,13 @@ namespace {
 
 }  // namespace
 
+bool search_would_tune(int dim, int ef, int64_t nq) {
+    const char *force = getenv("RNSM_SEARCH_VARIANT");
+    if (force && (force[0] == '0' || force[0] == '1')) return false;
+    if (nq < kTuneMin) return false;
+    return search_variant_for(dim, ef) < 0;
+}
+
 cudaError_t launch_search(const SearchArgs &a, cudaStream_t st) {
     if (a.nq <= 0) return cudaSuccess;
     if (!search_dim_supported(a.dim)) return cudaErrorInvalidValue;

@@ -264,6 +264,28 @@ def test_merge_batched_plan_with_shared_sources_exact(rn, flags):
     assert gst["pivots"] == wst["pivots"] and gst["followers"] == wst["followers"]
 
 
+def test_merge_graph_mode_captures_then_replays(rn):
+    # RNSM_FLAG_GRAPH: the first call captures S4..S7 of the plan in a CUDA graph,
+    # the second replays it; both equal the eager executor
+    sizes = [800, 1200, 650, 1000]
+    segs = [gen.sift_like(n, 70 + i, d=32) for i, n in enumerate(sizes)]
+    gs = [oracle.build_graph(s, 16, 32, 1.2) for s in segs]
+    plan = [(2, 0), (0, 1), (3, 1), (2, 3)]
+    tsegs = [(dev(sg), dev(g), e) for sg, (g, e) in zip(segs, gs)]
+    cplan = [(a, b, 0.0) for a, b in plan]
+    want, sw = rn.merge(tsegs, rn.params(16, 32, 1.2), cplan)
+    got1, s1 = rn.merge(tsegs, rn.params(16, 32, 1.2, flags=rn.FLAG_GRAPH), cplan)
+    got2, s2 = rn.merge(tsegs, rn.params(16, 32, 1.2, flags=rn.FLAG_GRAPH), cplan)
+    np.testing.assert_array_equal(host(got1), host(want))
+    np.testing.assert_array_equal(host(got2), host(want))
+    for st in (s1, s2):
+        assert st["reverse_edges"] == sw["reverse_edges"] and st["ndc"] == sw["ndc"]
+        assert st["pivots"] == sw["pivots"]
+    assert s2["launches"] == s1["launches"] > 0
+    ref, _ = oracle.rnsm_merge(segs, [g for g, _ in gs], [e for _, e in gs], plan, 16, 32, 1.2)
+    np.testing.assert_array_equal(host(got2), ref)
+
+
 def test_merge_float_data_recall_within_tolerance(rn):
     segs, Q = gen.tiny_case()
     gs = [oracle.build_graph(s, 16, 32, 1.2) for s in segs]
