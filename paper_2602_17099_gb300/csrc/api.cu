@@ -130,15 +130,20 @@ struct Ctl {
 struct QuantBufs {
     int32_t prec = 0;
     void *q = nullptr;
+    void *qlo = nullptr;   // two-term BF16 tiles of inner-product rows: the low terms
     float *scale = nullptr, *err = nullptr, *norm = nullptr;
 };
 
-void take_quant(Bump &b, int64_t n, int32_t dim, int32_t prec, QuantBufs &qb) {
+void take_quant(Bump &b, int64_t n, int32_t dim, int32_t prec, int32_t metric, QuantBufs &qb) {
     qb.prec = prec;
     qb.q = nullptr;
+    qb.qlo = nullptr;
     if (prec == 0) return;
-    if (prune_tc_terms(dim, prec) == 2) return;   // the split tile stages the FP32 rows
+    const int terms = prune_tc_terms(dim, prec);
+    // L2 two-term tiles centre the FP32 rows on each owner; they store nothing
+    if (terms == 2 && metric == RNSM_METRIC_L2) return;
     qb.q = b.take<char>((size_t)n * dim * (prec == 2 ? 1 : 2));
+    if (terms == 2) qb.qlo = b.take<char>((size_t)n * dim * 2);
     qb.scale = b.take<float>(n);
     qb.err = b.take<float>(n);
     qb.norm = b.take<float>(n);
@@ -151,6 +156,7 @@ void apply_quant(PruneArgs &a, const QuantBufs *qb, unsigned long long *rechecks
     a.tile_err = tile_err;
     a.prec = qb->prec;
     a.qrows = qb->q;
+    a.qrows_lo = qb->qlo;
     a.qscale = qb->scale;
     a.qerr = qb->err;
     a.qnorm = qb->norm;
@@ -567,10 +573,10 @@ rnsm_status rnsm_prune(const float *vecs, int64_t n, int32_t dim, const int32_t 
     Ctl c;
     QuantBufs qb;
     take_ctl(b, c, nv);
-    take_quant(b, n, dim, qprec, qb);
+    take_quant(b, n, dim, qprec, metric, qb);
     TRY(ws_acquire(b.off, b));
     take_ctl(b, c, nv);
-    take_quant(b, n, dim, qprec, qb);
+    take_quant(b, n, dim, qprec, metric, qb);
     TRY(ctl_reset(c, st));
     TRY(validate_on_device(vecs, n, dim, nullptr, 0, c, st));
     CK(launch_validate_ids(owners, nv, n, 0, c.err, st));
@@ -597,7 +603,7 @@ rnsm_status rnsm_prune(const float *vecs, int64_t n, int32_t dim, const int32_t 
     a.out = out;
     a.out_by_index = 1;
     a.err = c.err;
-    if (qb.q) CK(launch_quantize(tab, n, dim, qprec, qb.q, qb.scale, qb.err, qb.norm, st));
+    if (qb.q) CK(launch_quantize(tab, n, dim, qprec, qb.q, qb.qlo, qb.scale, qb.err, qb.norm, st));
     apply_quant(a, &qb, c.rechecks);
     TRY(run_prune(a, c.work + 8, c, st));
     TRY(check_err_word(c, st));
@@ -819,7 +825,7 @@ void carve_merge(Bump &b, const rnsm_params &p, int64_t nmax, int64_t n_all, int
     m.jobs5 = b.take<SearchJob>(n_jobs + 1);
     m.rev_counts = b.take<unsigned long long>(n_jobs + 1);
     take_rev(b, nmax, nmax * p.R, m.rev);
-    take_quant(b, n_all, dim, qprec, m.qb);
+    take_quant(b, n_all, dim, qprec, p.metric, m.qb);
 }
 
 // Rows of result table needed by the largest group of the plan.
@@ -1018,7 +1024,8 @@ rnsm_status rnsm_merge(const rnsm_segment *segs, int32_t m, const rnsm_params *p
         CK(launch_init_lists(segs[s].adj, segs[s].n, segs[s].r_in, (int32_t)tab.off[s],
                              out_adj + tab.off[s] * p.R, p.R, st));
     if (mb.qb.q)  // BF16 / E4M3 copies of every row for the one-term tensor-core tiles
-        CK(launch_quantize(tab, off, dim, qprec, mb.qb.q, mb.qb.scale, mb.qb.err, mb.qb.norm, st));
+        CK(launch_quantize(tab, off, dim, qprec, mb.qb.q, mb.qb.qlo, mb.qb.scale, mb.qb.err,
+                           mb.qb.norm, st));
     tm.end(t_init);
 
     const int32_t ks = p.ef_slide < p.L ? p.ef_slide : p.L;

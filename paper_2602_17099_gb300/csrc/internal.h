@@ -112,6 +112,7 @@ struct PruneArgs {
     unsigned long long *ecount;
     int32_t prec;             // 0 FP32; 1 BF16 / 2 FP8 tiles on the tensor cores
     const void *qrows;        // quantized rows by global id [N * dim] (BF16 or E4M3)
+    const void *qrows_lo;     // nullable: BF16 low terms lo = bf16(x - hi), qrows holding hi
     const float *qscale;      // FP8 per-row scale
     const float *qerr;        // residual norms ||x - x~||
     const float *qnorm;       // row norms ||x||
@@ -136,8 +137,10 @@ int prune_tc_max_pool();
 cudaError_t launch_prune_tc(const PruneArgs &a, cudaStream_t st);
 // Rows of the segment table to BF16 (prec 1) or E4M3 with per-row scale (prec 2),
 // plus residual norms and row norms.
+// With q_lo (BF16 only) the rows are split into q = bf16(x) and q_lo = bf16(x - q)
+// and err is ||x - q - q_lo||.
 cudaError_t launch_quantize(const SegTable &segs, int64_t n, int32_t dim, int prec, void *q,
-                            float *scale, float *err, float *norm, cudaStream_t st);
+                            void *q_lo, float *scale, float *err, float *norm, cudaStream_t st);
 
 // Counting sort of (key, val) pairs by key into CSR (K3).
 // keys/vals [cap], the number of valid pairs at *count (device) or n_host.

@@ -74,9 +74,7 @@ __device__ __forceinline__ void carve(unsigned char *p, int rows_cap, int pool_c
     s.stile = slow ? reinterpret_cast<float *>(s.kid + R) : nullptr;
 }
 
-__device__ __forceinline__ float chain(float acc, float4 a, float4 b, int metric) {
-    return metric == 0 ? l2_acc(acc, a, b) : ip_acc(acc, a, b);
-}
+
 
 // Stages float4 columns [d0/4, d0/4 + dc4) of rows [0, nrows4) (rptr) into
 // smem; eight loads are issued before their stores so they overlap.
@@ -235,13 +233,13 @@ __global__ void __launch_bounds__(kThreads) prune_kernel(const PruneArgs a, int 
                     bbs[t] = -1;
                 }
             }
-            float acc[kNBF][4][4];
+            f2_t acc[kNBF][4][4];
 #pragma unroll
             for (int t = 0; t < kNBF; ++t)
 #pragma unroll
                 for (int p = 0; p < 4; ++p)
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) acc[t][p][q] = 0.f;
+                    for (int q = 0; q < 4; ++q) acc[t][p][q] = 0ull;
             __syncthreads();
             for (int d0 = 0; d0 < dim; d0 += kDch) {
                 const int dc4 = min(kDch, dim - d0) >> 2;
@@ -250,10 +248,10 @@ __global__ void __launch_bounds__(kThreads) prune_kernel(const PruneArgs a, int 
 #pragma unroll
                 for (int t = 0; t < kNBF; ++t) {
                     if (bas[t] < 0) continue;
-                    const float4 *ra = s.rows + srow4(4 * bas[t]);
-                    const float4 *rb = s.rows + srow4(4 * bbs[t]);
+                    const ulonglong2 *ra = reinterpret_cast<const ulonglong2 *>(s.rows + srow4(4 * bas[t]));
+                    const ulonglong2 *rb = reinterpret_cast<const ulonglong2 *>(s.rows + srow4(4 * bbs[t]));
                     for (int f = 0; f < dc4; ++f) {
-                        float4 xa[4], xb[4];
+                        ulonglong2 xa[4], xb[4];
 #pragma unroll
                         for (int p = 0; p < 4; ++p) {
                             xa[p] = ra[p * (kDch / 4 + 1) + f];
@@ -263,7 +261,7 @@ __global__ void __launch_bounds__(kThreads) prune_kernel(const PruneArgs a, int 
                         for (int p = 0; p < 4; ++p)
 #pragma unroll
                             for (int q = 0; q < 4; ++q)
-                                acc[t][p][q] = chain(acc[t][p][q], xa[p], xb[q], metric);
+                                acc[t][p][q] = chain2(acc[t][p][q], xa[p], xb[q], metric);
                     }
                 }
                 __syncthreads();
@@ -278,8 +276,7 @@ __global__ void __launch_bounds__(kThreads) prune_kernel(const PruneArgs a, int 
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
                         const int ra = 4 * bas[t] + p, rb = 4 * bbs[t] + q;
-                        if (ra < rb && rb < nrows)
-                            T[tri(ra, rb, nrows)] = metric == 0 ? acc[t][p][q] : 1.0f - acc[t][p][q];
+                        if (ra < rb && rb < nrows) T[tri(ra, rb, nrows)] = chain2_final(acc[t][p][q], metric);
                     }
             }
             __syncthreads();
@@ -324,12 +321,8 @@ __global__ void __launch_bounds__(kThreads) prune_kernel(const PruneArgs a, int 
             // ---------------- slow path: large pools ----------------
             // d(v, c): one thread per candidate, the same chain from global memory
             const float *orow = seg_row(a.segs, owner, dim);
-            for (int j = tid; j < np; j += kThreads) {
-                const float *row = seg_row(a.segs, s.pid[j], dim);
-                float acc = 0.f;
-                for (int f = 0; f < F4; ++f) acc = chain(acc, ldg4(orow + 4 * f), ldg4(row + 4 * f), metric);
-                s.pd[j] = metric == 0 ? acc : 1.0f - acc;
-            }
+            for (int j = tid; j < np; j += kThreads)
+                s.pd[j] = prune_dist(orow, seg_row(a.segs, s.pid[j], dim), dim, metric);
             __syncthreads();
             sort_pool(s, npad);
             if (a.keep_all_if_fit && np <= R) {
@@ -348,13 +341,13 @@ __global__ void __launch_bounds__(kThreads) prune_kernel(const PruneArgs a, int 
                     }
                     for (int j = tid; j < nk; j += kThreads) s.krow[j] = j;
                     __syncthreads();
-                    float acc[kNBS][4][4];
+                    f2_t acc[kNBS][4][4];
 #pragma unroll
                     for (int t = 0; t < kNBS; ++t)
 #pragma unroll
                         for (int p = 0; p < 4; ++p)
 #pragma unroll
-                            for (int q = 0; q < 4; ++q) acc[t][p][q] = 0.f;
+                            for (int q = 0; q < 4; ++q) acc[t][p][q] = 0ull;
                     for (int d0 = 0; d0 < dim; d0 += kDch) {
                         const int dc4 = min(kDch, dim - d0) >> 2;
                         stage(s, 4 * nA, d0, dc4);
@@ -364,16 +357,16 @@ __global__ void __launch_bounds__(kThreads) prune_kernel(const PruneArgs a, int 
                             const int b = tid + kThreads * t;
                             if (b >= nblk) continue;
                             const int ba = b / nB, bb = b - ba * nB;
-                            const float4 *ra[4], *rb[4];
+                            const ulonglong2 *ra[4], *rb[4];
 #pragma unroll
                             for (int p = 0; p < 4; ++p) {
-                                ra[p] = s.rows + srow4(ba + nA * p);
+                                ra[p] = reinterpret_cast<const ulonglong2 *>(s.rows + srow4(ba + nA * p));
                                 int rbi = nk + bb + nB * p;
                                 if (rbi >= 4 * nA) rbi = 0;
-                                rb[p] = s.rows + srow4(rbi);
+                                rb[p] = reinterpret_cast<const ulonglong2 *>(s.rows + srow4(rbi));
                             }
                             for (int f = 0; f < dc4; ++f) {
-                                float4 xa[4], xb[4];
+                                ulonglong2 xa[4], xb[4];
 #pragma unroll
                                 for (int p = 0; p < 4; ++p) {
                                     xa[p] = ra[p][f];
@@ -383,7 +376,7 @@ __global__ void __launch_bounds__(kThreads) prune_kernel(const PruneArgs a, int 
                                 for (int p = 0; p < 4; ++p)
 #pragma unroll
                                     for (int q = 0; q < 4; ++q)
-                                        acc[t][p][q] = chain(acc[t][p][q], xa[p], xb[q], metric);
+                                        acc[t][p][q] = chain2(acc[t][p][q], xa[p], xb[q], metric);
                             }
                         }
                         __syncthreads();
@@ -399,8 +392,7 @@ __global__ void __launch_bounds__(kThreads) prune_kernel(const PruneArgs a, int 
                             for (int q = 0; q < 4; ++q) {
                                 const int ar = ba + nA * p, bc = bb + nB * q;
                                 if (ar < nrows && bc < cs && ar < nk + bc)
-                                    s.stile[ar * kTile + bc] =
-                                        metric == 0 ? acc[t][p][q] : 1.0f - acc[t][p][q];
+                                    s.stile[ar * kTile + bc] = chain2_final(acc[t][p][q], metric);
                             }
                     }
                     __syncthreads();
@@ -478,10 +470,10 @@ __global__ void __launch_bounds__(kThreads) prune_kernel(const PruneArgs a, int 
 // duplicates (equal keys rank next to each other) are skipped.  Larger pools
 // are appended to an overflow list for prune_kernel.
 
-constexpr int kSmallThreads = 128;
+constexpr int kSmallThreads = 160;    // one 4x4 block of the triangle per thread
 constexpr int kSmallMax = 64;
 constexpr int kSmallRows = 68;      // owner + 64, rounded up to 4
-constexpr int kSmallNB = 2;         // 17*18/2 = 153 blocks over 128 threads
+constexpr int kSmallNB = 1;         // 17*18/2 = 153 blocks over 160 threads
 
 struct SmallSmem {
     float4 rows[rows_float4(kSmallRows)];
@@ -495,7 +487,7 @@ struct SmallSmem {
     uint32_t occ[2 * kSmallMax];
 };
 
-__global__ void __launch_bounds__(kSmallThreads, 5) prune_small_kernel(const PruneArgs a, int chunk) {
+__global__ void __launch_bounds__(kSmallThreads, 3) prune_small_kernel(const PruneArgs a, int chunk) {
     __shared__ __align__(16) SmallSmem s;
     __shared__ int64_t sh_i;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -560,13 +552,13 @@ __global__ void __launch_bounds__(kSmallThreads, 5) prune_small_kernel(const Pru
                 bbs[t] = -1;
             }
         }
-        float acc[kSmallNB][4][4];
+        f2_t acc[kSmallNB][4][4];
 #pragma unroll
         for (int t = 0; t < kSmallNB; ++t)
 #pragma unroll
             for (int p = 0; p < 4; ++p)
 #pragma unroll
-                for (int q = 0; q < 4; ++q) acc[t][p][q] = 0.f;
+                for (int q = 0; q < 4; ++q) acc[t][p][q] = 0ull;
         for (int d0 = 0; d0 < dim; d0 += kDch) {
             const int dc4 = min(kDch, dim - d0) >> 2;
             stage_rows<kSmallThreads>(s.rows, s.rptr, 4 * nB, d0, dc4);
@@ -574,10 +566,10 @@ __global__ void __launch_bounds__(kSmallThreads, 5) prune_small_kernel(const Pru
 #pragma unroll
             for (int t = 0; t < kSmallNB; ++t) {
                 if (bas[t] < 0) continue;
-                const float4 *ra = s.rows + srow4(4 * bas[t]);
-                const float4 *rb = s.rows + srow4(4 * bbs[t]);
+                const ulonglong2 *ra = reinterpret_cast<const ulonglong2 *>(s.rows + srow4(4 * bas[t]));
+                const ulonglong2 *rb = reinterpret_cast<const ulonglong2 *>(s.rows + srow4(4 * bbs[t]));
                 for (int f = 0; f < dc4; ++f) {
-                    float4 xa[4], xb[4];
+                    ulonglong2 xa[4], xb[4];
 #pragma unroll
                     for (int p = 0; p < 4; ++p) {
                         xa[p] = ra[p * (kDch / 4 + 1) + f];
@@ -587,7 +579,7 @@ __global__ void __launch_bounds__(kSmallThreads, 5) prune_small_kernel(const Pru
                     for (int p = 0; p < 4; ++p)
 #pragma unroll
                         for (int q = 0; q < 4; ++q)
-                            acc[t][p][q] = chain(acc[t][p][q], xa[p], xb[q], metric);
+                            acc[t][p][q] = chain2(acc[t][p][q], xa[p], xb[q], metric);
                 }
             }
             __syncthreads();
@@ -601,8 +593,7 @@ __global__ void __launch_bounds__(kSmallThreads, 5) prune_small_kernel(const Pru
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     const int ra = 4 * bas[t] + p, rb = 4 * bbs[t] + q;
-                    if (ra < rb && rb < nrows)
-                        T[tri(ra, rb, nrows)] = metric == 0 ? acc[t][p][q] : 1.0f - acc[t][p][q];
+                    if (ra < rb && rb < nrows) T[tri(ra, rb, nrows)] = chain2_final(acc[t][p][q], metric);
                 }
         }
         __syncthreads();

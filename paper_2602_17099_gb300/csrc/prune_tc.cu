@@ -20,7 +20,7 @@
 // where for L2 every staged row is centred on the owner (x_r - x_v), so the
 // Gram entries are of the size of the distances themselves and the tile is
 // free of cancellation.  A bound B(i,j) >= |d~(i,j) - d(i,j)|, with d the
-// FP32 prune's value (the fixed FP32 chain over the dimensions), covers the
+// FP32 prune's value (its fixed pair of FP32 chains over the dimensions), covers the
 // quantisation error of the staged rows (their error norms), the FP32
 // accumulation of the Gram, and the chain's own rounding.  A candidate whose
 // owner-distance interval overlaps another's gets its exact FP32 owner
@@ -62,27 +62,10 @@ constexpr uint64_t kWaitNs = 1000000000ull;   // an MMA group takes microseconds
 
 static_assert(kRawBytes / 4 >= kPairsMax, "the undecided list lives in a raw buffer");
 
-// The FP32 prune's distance: one fmaf chain over the dimensions in order
-// (loads issued eight float4 ahead; the arithmetic order is unchanged).
-__device__ float exact_dist(const float *a, const float *b, int dim, int metric) {
-    float acc = 0.f;
-    const int F4 = dim >> 2;
-    int f = 0;
-    for (; f + 8 <= F4; f += 8) {
-        float4 x[8], y[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            x[u] = ldg4(a + 4 * (f + u));
-            y[u] = ldg4(b + 4 * (f + u));
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) acc = metric == 0 ? l2_acc(acc, x[u], y[u]) : ip_acc(acc, x[u], y[u]);
-    }
-    for (; f < F4; ++f) {
-        const float4 x = ldg4(a + 4 * f), y = ldg4(b + 4 * f);
-        acc = metric == 0 ? l2_acc(acc, x, y) : ip_acc(acc, x, y);
-    }
-    return metric == 0 ? acc : 1.0f - acc;
+// The FP32 prune's distance (the two-chain definition shared with the FP32
+// prune kernels, common.cuh).
+__device__ __forceinline__ float exact_dist(const float *a, const float *b, int dim, int metric) {
+    return prune_dist(a, b, dim, metric);
 }
 
 // The same distance in FP64 (error statistics only).
@@ -122,7 +105,7 @@ struct TcSmem {
     int32_t live[kMaxC];        // valid and the first of its id in that order
     int32_t kept[64];
     int n_undecided;
-    uint64_t bar;
+    uint64_t bar[2];            // MMA completion, one per tile buffer
     uint32_t tmem_slot;
 };
 
@@ -158,13 +141,15 @@ __global__ void __launch_bounds__(kThreads, 2) prune_tc_kernel(const PruneArgs a
     // tiles (rnsm_stats.tile_error) measure the share of the bound actually used.
     const int n_instr = (kTerms == 2 ? 3 : 1) * (kFp8 ? dim / 32 : dim / 16);
     const float eps_c = 1.01f * (float)(n_instr + 1) * 2.384185791e-07f;
-    // the FP32 chain: (dim + 2) u (sum of |terms|), u = 2^-24 (one rounding per fmaf, plus
-    // the rounded difference inside each L2 term), times a margin
+    // the FP32 distance (two chains of dim / 2 terms and their sum): at most
+    // (dim + 2) u (sum of |terms|), u = 2^-24 (one rounding per fmaf, the rounded
+    // difference inside each L2 term, the final sum), times a margin
     const float gam = 1.01f * (float)(dim + 2) * 5.9604645e-08f;
     const unsigned char *Q = static_cast<const unsigned char *>(a.qrows);
 
     if (tid == 0) {
-        tc::mbar_init(&s.bar, 1);
+        tc::mbar_init(&s.bar[0], 1);
+        tc::mbar_init(&s.bar[1], 1);
         sh_fail = 0;
     }
     if (warp == 0) {
@@ -180,17 +165,48 @@ __global__ void __launch_bounds__(kThreads, 2) prune_tc_kernel(const PruneArgs a
     // and occ[c] (bit s set if kept s would drop c)
     uint32_t *const undecided = reinterpret_cast<uint32_t *>(raw0);
     uint32_t (*const occ)[4] = reinterpret_cast<uint32_t (*)[4]>(raw0 + kRawBytes);
-    uint32_t phase = 0;
     unsigned long long rechecks = 0;
-
-    // waits for the MMAs committed last; false after kWaitNs (then the CTA
-    // records the error and stops)
-    auto wait_mma = [&]() -> bool {
-        const bool ok = tc::mbar_wait_bounded(&s.bar, phase, kWaitNs);
+    // IP rows whose tile terms the library stored (the quantized copies, or hi and lo
+    // for two terms) go straight from global memory into the tile: no conversion
+    const bool direct = metric != 0 && (kTerms == 1 || a.qrows_lo != nullptr);
+    const unsigned char *QL = static_cast<const unsigned char *>(a.qrows_lo);
+    const int q_bytes = dim * (kFp8 ? 1 : 2);      // bytes of one stored term row
+    // Each tile buffer has its own mbarrier, so at most one commit per barrier is
+    // outstanding and a parity wait is unambiguous.
+    uint32_t ph0 = 0, ph1 = 0;          // the phase parity each barrier completes next
+    bool pend0 = false, pend1 = false;  // a commit not waited for yet
+    // waits for barrier b; false after kWaitNs (the CTA records the error and stops)
+    auto wait_bar = [&](int b) -> bool {
+        const bool ok = tc::mbar_wait_bounded(&s.bar[b], b ? ph1 : ph0, kWaitNs);
         const int timed_out = __syncthreads_or(!ok);
-        phase ^= 1u;
-        if (timed_out && tid == 0) { atomicOr(a.err, 64); sh_fail = 1; }
-        return !timed_out;
+        if (timed_out) {
+            if (tid == 0) { atomicOr(a.err, 64); sh_fail = 1; }
+            return false;
+        }
+        if (b) { ph1 ^= 1u; pend1 = false; } else { ph0 ^= 1u; pend0 = false; }
+        return true;
+    };
+    // the MMAs of K-chunk kc (tile bytes kb per row and term) from tile buffer tb
+    auto issue_mma = [&](int kc, int kb, uint32_t tb, int bar) {
+        if (tid == 0) {
+            const uint32_t idesc = tc::instr_desc(kFp8 ? 0u : 1u, kM, kN);
+            for (int k = 0; k < kb / 32; ++k) {
+                const uint64_t dh = tc::smem_desc(tb + k * 256, 128, kSBO);
+                const uint32_t acc = (kc > 0 || k > 0) ? 1u : 0u;
+                if (kFp8) {
+                    tc::mma_fp8(taddr, dh, dh, idesc, acc);
+                } else {
+                    tc::mma_bf16(taddr, dh, dh, idesc, acc);
+                    if (kTerms == 2) {
+                        const uint64_t dl = tc::smem_desc(tb + kRegion + k * 256, 128, kSBO);
+                        tc::mma_bf16(taddr, dl, dh, idesc, 1u);   // lo * hi
+                        tc::mma_bf16(taddr, dh, dl, idesc, 1u);   // hi * lo
+                    }
+                }
+            }
+            if (!a.test_withhold_commit) tc::mma_commit(&s.bar[bar]);
+        }
+        if (bar) pend1 = true; else pend0 = true;
     };
 
     for (;;) {
@@ -285,7 +301,49 @@ __global__ void __launch_bounds__(kThreads, 2) prune_tc_kernel(const PruneArgs a
             }
             tc::cp_async_commit();
         };
+        // direct path: chunk kc + 1 lands in the other tile buffer while chunk kc is
+        // multiplied
+        auto prefetch_direct = [&](int kc) {
+            unsigned char *tb = tile + (kc & 1) * kTileBytes;
+            const int kb = min(kTermB, q_bytes - kc * kTermB);
+            const int units = kb >> 4;
+            for (int e = tid; e < (nc + 1) * units; e += kThreads) {
+                const int rr0 = e / units, u = e - rr0 * units;
+                const bool own = rr0 == nc;
+                const int32_t g = own ? owner : s.pid[rr0];
+                if (g < 0) continue;   // an empty slot's tile row is never read
+                const int r = own ? kOwnerRow : rr0;
+                const uint32_t so = (uint32_t)((r >> 3) * kSBO + u * 128 + (r & 7) * 16);
+                const int64_t off = (int64_t)g * q_bytes + (int64_t)kc * kTermB + 16 * u;
+                tc::cp_async16(tb + so, Q + off);
+                if (kTerms == 2) tc::cp_async16(tb + kRegion + so, QL + off);
+            }
+            tc::cp_async_commit();
+        };
         bool failed = false;
+        if (direct) {
+            prefetch_direct(0);
+            for (int kc = 0; kc < n_chunks; ++kc) {
+                const int b = kc & 1;
+                if (kc + 1 < n_chunks) {
+                    if ((b ? pend0 : pend1) && !wait_bar(b ^ 1)) {   // MMA kc - 1 read it
+                        tc::cp_async_wait<0>();
+                        failed = true;
+                        break;
+                    }
+                    prefetch_direct(kc + 1);
+                    tc::cp_async_wait<1>();
+                } else {
+                    tc::cp_async_wait<0>();
+                }
+                tc::fence_async_shared();
+                tc::fence_before_sync();
+                __syncthreads();
+                tc::fence_after_sync();
+                issue_mma(kc, min(kTermB, q_bytes - kc * kTermB), tbase + b * kTileBytes, b);
+            }
+        }
+        if (!direct) {
         prefetch(0);
         for (int kc = 0; kc < n_chunks; ++kc) {
             if (kc + 1 < n_chunks) {
@@ -295,7 +353,7 @@ __global__ void __launch_bounds__(kThreads, 2) prune_tc_kernel(const PruneArgs a
                 tc::cp_async_wait<0>();
             }
             __syncthreads();                                          // raw chunk kc is in
-            if (kc > 0 && !wait_mma()) {                            // the tile is free
+            if (pend0 && !wait_bar(0)) {                             // the tile is free
                 tc::cp_async_wait<0>();
                 failed = true;
                 break;
@@ -403,24 +461,8 @@ __global__ void __launch_bounds__(kThreads, 2) prune_tc_kernel(const PruneArgs a
             tc::fence_before_sync();
             __syncthreads();
             tc::fence_after_sync();
-            if (tid == 0) {
-                const uint32_t idesc = tc::instr_desc(kFp8 ? 0u : 1u, kM, kN);
-                for (int k = 0; k < kb / 32; ++k) {
-                    const uint64_t dh = tc::smem_desc(tbase + k * 256, 128, kSBO);
-                    const uint32_t acc = (kc > 0 || k > 0) ? 1u : 0u;
-                    if (kFp8) {
-                        tc::mma_fp8(taddr, dh, dh, idesc, acc);
-                    } else {
-                        tc::mma_bf16(taddr, dh, dh, idesc, acc);
-                        if (kTerms == 2) {
-                            const uint64_t dl = tc::smem_desc(tbase + kRegion + k * 256, 128, kSBO);
-                            tc::mma_bf16(taddr, dl, dh, idesc, 1u);   // lo * hi
-                            tc::mma_bf16(taddr, dh, dl, idesc, 1u);   // hi * lo
-                        }
-                    }
-                }
-                if (!a.test_withhold_commit) tc::mma_commit(&s.bar);
-            }
+            issue_mma(kc, kb, tbase, 0);
+        }
         }
         if (failed) break;
         // error norms of the staged rows (the staging reductions are complete)
@@ -428,7 +470,10 @@ __global__ void __launch_bounds__(kThreads, 2) prune_tc_kernel(const PruneArgs a
             const bool own = r == kMaxC;
             const int32_t g = own ? owner : (r < nc ? s.pid[r] : -1);
             float E = 0.f;
-            if (g >= 0) {
+            if (g >= 0 && direct) {
+                E = a.qerr[g];   // stored residual: x - x~ (one term) or x - hi - lo
+                s.nr[r] = a.qnorm[g];
+            } else if (g >= 0) {
                 const float res = s.res[r];
                 const float rs = res > 0.f ? sqrtf(res) * 1.001f : 0.f;   // atomic order varies
                 if (kTerms == 1) {
@@ -442,7 +487,7 @@ __global__ void __launch_bounds__(kThreads, 2) prune_tc_kernel(const PruneArgs a
             }
             s.E[r] = E + 1e-30f;
         }
-        if (!wait_mma()) break;
+        if ((pend0 && !wait_bar(0)) || (pend1 && !wait_bar(1))) break;
         tc::fence_after_sync();
 
         // 3. diagonal and owner column of the tile
@@ -713,18 +758,22 @@ __global__ void __launch_bounds__(kThreads, 2) prune_tc_kernel(const PruneArgs a
         if (sh_fail) break;
     }
     if (rechecks && a.rechecks) atomicAdd(a.rechecks, rechecks);
-    if (sh_fail)  // give an MMA that did not finish a second bounded chance before freeing TMEM
-        tc::mbar_wait_bounded(&s.bar, phase ^ 1u, kWaitNs);
+    if (sh_fail) {  // give MMAs that did not finish a second bounded chance before freeing TMEM
+        if (pend0) tc::mbar_wait_bounded(&s.bar[0], ph0, kWaitNs);
+        if (pend1) tc::mbar_wait_bounded(&s.bar[1], ph1, kWaitNs);
+    }
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(taddr, kTmemCols);
 }
 
 // Row quantisation: BF16 (round to nearest) or E4M3 with a per-row scale
-// (max |x| / 448), the residual norm ||x - x~|| (rounded up) and ||x||.
-template <bool kFp8>
-__global__ void quantize_kernel(SegTable segs, int64_t n, int32_t dim, void *q, float *scale,
-                                float *err, float *norm) {
+// (max |x| / 448), the residual norm ||x - x~|| (rounded up) and ||x||.  With
+// kSplit (BF16) the row is stored as hi = bf16(x) and lo = bf16(x - hi) and
+// the residual is ||x - hi - lo||.
+template <bool kFp8, bool kSplit>
+__global__ void quantize_kernel(SegTable segs, int64_t n, int32_t dim, void *q, void *q_lo,
+                                float *scale, float *err, float *norm) {
     const int lane = threadIdx.x & 31;
     const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -745,17 +794,21 @@ __global__ void quantize_kernel(SegTable segs, int64_t n, int32_t dim, void *q, 
         float ee = 0.f;
         for (int k = lane; k < dim; k += 32) {
             const float v = x[k];
-            float back;
+            float dlt;
             if (kFp8) {
                 const __nv_fp8_e4m3 t(v / sc);
                 reinterpret_cast<__nv_fp8_e4m3 *>(q)[r * dim + k] = t;
-                back = sc * static_cast<float>(t);
+                dlt = v - sc * static_cast<float>(t);
             } else {
                 const __nv_bfloat16 t = __float2bfloat16_rn(v);
                 reinterpret_cast<__nv_bfloat16 *>(q)[r * dim + k] = t;
-                back = __bfloat162float(t);
+                dlt = v - __bfloat162float(t);   // exact
+                if (kSplit) {
+                    const __nv_bfloat16 t2 = __float2bfloat16_rn(dlt);
+                    reinterpret_cast<__nv_bfloat16 *>(q_lo)[r * dim + k] = t2;
+                    dlt -= __bfloat162float(t2);   // exact
+                }
             }
-            const float dlt = v - back;
             ee = fmaf(dlt, dlt, ee);
         }
 #pragma unroll
@@ -825,12 +878,16 @@ cudaError_t launch_prune_tc(const PruneArgs &in, cudaStream_t st) {
 }
 
 cudaError_t launch_quantize(const SegTable &segs, int64_t n, int32_t dim, int prec, void *q,
-                            float *scale, float *err, float *norm, cudaStream_t st) {
+                            void *q_lo, float *scale, float *err, float *norm, cudaStream_t st) {
     int64_t g = (n * 32 + 255) / 256;
     if (g > 16384) g = 16384;
     if (g < 1) g = 1;
-    if (prec == 2) quantize_kernel<true><<<(unsigned)g, 256, 0, st>>>(segs, n, dim, q, scale, err, norm);
-    else quantize_kernel<false><<<(unsigned)g, 256, 0, st>>>(segs, n, dim, q, scale, err, norm);
+    if (prec == 2)
+        quantize_kernel<true, false><<<(unsigned)g, 256, 0, st>>>(segs, n, dim, q, nullptr, scale, err, norm);
+    else if (q_lo)
+        quantize_kernel<false, true><<<(unsigned)g, 256, 0, st>>>(segs, n, dim, q, q_lo, scale, err, norm);
+    else
+        quantize_kernel<false, false><<<(unsigned)g, 256, 0, st>>>(segs, n, dim, q, nullptr, scale, err, norm);
     note_launches(1);
     return cudaGetLastError();
 }
