@@ -78,6 +78,16 @@ def _embed(scale, nq):
     return [X[p_].copy() for p_ in parts], X[4 * n:].copy()
 
 
+def _deep50(scale, nq):
+    """50 DEEP-like segments, 100M rows at full size, drawn on the GPU (38 GB)."""
+    import torch
+    total = max(50_000, int(100_000_000 * scale))
+    sizes = gen.lognormal_sizes(50, total, max(1000, int(500_000 * scale)),
+                                max(4000, int(5_000_000 * scale)), seed=9)
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    return gen.deep_like_gpu_segments(total, nq, 9, sizes, 1009, device=dev)
+
+
 WORKLOADS = {
     "sift2x500k": Workload("sift2x500k", "sift-like 2x500k d128 L2 R32 L64 alpha1.2", 128, 32, 64,
                            1.2, L2_METRIC, _sift, False, ("bf16", "fp8"), 0.1),
@@ -87,7 +97,15 @@ WORKLOADS = {
     "embed4x250k": Workload("embed4x250k", "embedding-like 4x250k d768 IP R64 L128 alpha1.2, "
                             "MOS plan", 768, 64, 128, 1.2, IP_METRIC, _embed, True,
                             ("bf16", "fp8"), 0.01),
+    "deep50x100m": Workload("deep50x100m", "deep-like 50 segments (lognormal 0.5M-5M, 100M total, "
+                            "cluster partition, drawn on the GPU) d96 L2 R32 L64 alpha1.2, MOS plan",
+                            96, 32, 64, 1.2, L2_METRIC, _deep50, True, ("bf16",), 0.01),
 }
+
+
+def to_host(x):
+    """numpy view of a workload array (device tensors are copied to the host)."""
+    return x if isinstance(x, np.ndarray) else x.cpu().numpy()
 
 
 def dist_env():
@@ -175,7 +193,9 @@ class ClockSampler:
 # ------------------------------------------------------------- oracle arm
 
 def centroids_of(segs):
-    return np.stack([s_.mean(axis=0, dtype=np.float64) for s_ in segs]).astype(np.float32)
+    if isinstance(segs[0], np.ndarray):
+        return np.stack([s_.mean(axis=0, dtype=np.float64) for s_ in segs]).astype(np.float32)
+    return np.stack([s_.double().mean(0).cpu().numpy() for s_ in segs]).astype(np.float32)
 
 
 def host_plan(W, segs, planner):
@@ -191,6 +211,7 @@ def oracle_sample(W, args):
     ``W.oracle_scale`` of the full size, graphs built by the oracle (untimed)."""
     import oracle
     segs, _ = W.make(W.oracle_scale, 10)
+    segs = [to_host(s_) for s_ in segs]
     gs = [oracle.build_graph(s_, W.R, W.L, W.alpha, metric=W.metric) for s_ in segs]
     return oracle, segs, gs
 
@@ -277,38 +298,57 @@ def search_profile_traffic():
         return None
 
 
-def recall_at_10(rn, torch, W, Xd, adj, entry, Q, ef=64):
+def recall_at_10(rn, torch, W, Xd, adj, entry, Q, ef=64, chunk_rows=1 << 22, qb=64):
     """Tie-tolerant Recall@10 of the merged graph (evaluation only): a returned
-    id counts if its FP64 distance is within the true 10th-NN distance."""
-    Qd = torch.from_numpy(Q).cuda()
-    seeds = torch.full((len(Q), 1), entry, dtype=torch.int32, device="cuda")
+    id counts if its FP64 distance is within the true 10th-NN distance.  The
+    true neighbours come from a chunked FP32 scan (top 32 per query) re-ranked
+    in FP64."""
+    Qd = Q if torch.is_tensor(Q) else torch.from_numpy(Q)
+    Qd = Qd.cuda()
+    nq = Qd.shape[0]
+    seeds = torch.full((nq, 1), entry, dtype=torch.int32, device="cuda")
     ids, _, _ = rn.search(Xd, adj, Qd, seeds, ef, 10, metric=W.metric)
-    Xn = (Xd * Xd).sum(1)
+
+    def native(rows64, q64):
+        if W.metric == L2_METRIC:
+            return ((rows64 - q64[:, None, :]) ** 2).sum(-1)
+        return 1.0 - (rows64 * q64[:, None, :]).sum(-1)
+
     hit = 0
-    for b in range(0, len(Q), 256):
-        q = Qd[b:b + 256]
-        if W.metric == L2_METRIC:
-            approx = (q * q).sum(1, keepdim=True) + Xn[None] - 2.0 * (q @ Xd.T)
-        else:
-            approx = 1.0 - q @ Xd.T
-        cand = torch.topk(approx, 32, largest=False).indices          # exact re-rank in FP64
+    for b in range(0, nq, qb):
+        q = Qd[b:b + qb]
+        best_d = best_i = None
+        for c0 in range(0, Xd.shape[0], chunk_rows):
+            Xc = Xd[c0:c0 + chunk_rows]
+            if W.metric == L2_METRIC:
+                approx = (q * q).sum(1, keepdim=True) + (Xc * Xc).sum(1)[None] - 2.0 * (q @ Xc.T)
+            else:
+                approx = 1.0 - q @ Xc.T
+            dv, iv = torch.topk(approx, min(32, Xc.shape[0]), largest=False)
+            iv = iv + c0
+            if best_d is not None:
+                dv, iv = torch.cat([best_d, dv], 1), torch.cat([best_i, iv], 1)
+            sel = torch.topk(dv, min(32, dv.shape[1]), largest=False).indices
+            best_d, best_i = torch.gather(dv, 1, sel), torch.gather(iv, 1, sel)
         q64 = q.double()
-        ex = exact = None
-        rows = Xd[cand].double()
-        if W.metric == L2_METRIC:
-            exact = ((rows - q64[:, None, :]) ** 2).sum(-1)
-        else:
-            exact = 1.0 - (rows * q64[:, None, :]).sum(-1)
-        d10 = torch.sort(exact, dim=1).values[:, 9]
-        got = ids[b:b + 256]
-        g = Xd[got.clamp(min=0).long()].double()
-        if W.metric == L2_METRIC:
-            ex = ((g - q64[:, None, :]) ** 2).sum(-1)
-        else:
-            ex = 1.0 - (g * q64[:, None, :]).sum(-1)
+        d10 = torch.sort(native(Xd[best_i].double(), q64), dim=1).values[:, 9]
+        got = ids[b:b + qb]
+        ex = native(Xd[got.clamp(min=0).long()].double(), q64)
         tol = 1e-9 * d10.abs()[:, None] + 1e-12
         hit += ((ex <= d10[:, None] + tol) & (got >= 0)).sum().item()
-    return hit / (10 * len(Q))
+    return hit / (10 * nq)
+
+
+def concat_rows(torch, vd):
+    """The segments as one [N, d] table: a view when they already sit back to
+    back in one allocation (device-drawn workloads), else a copy."""
+    d = vd[0].shape[1]
+    p, off = vd[0].data_ptr(), 0
+    for v in vd:
+        if v.data_ptr() != p + off * d * 4 or not v.is_contiguous():
+            return torch.cat(vd)
+        off += v.shape[0]
+    return vd[0].as_strided((off, d), (d, 1))
 
 
 def run_ours(args, ws, rank, local):
@@ -333,7 +373,8 @@ def run_ours(args, ws, rank, local):
         segs, Q = W.make(args.scale, args.recall_queries)
     N = sum(len(s_) for s_ in segs)
     cen = centroids_of(segs)
-    vd = [torch.from_numpy(s_).cuda() for s_ in segs]
+    vd = [s_ if torch.is_tensor(s_) else torch.from_numpy(s_).cuda() for s_ in segs]
+    huge = N > 20_000_000   # tens of GB: fewer repetitions of the extra measurements
     t0 = time.perf_counter()
     graphs = [rn.build_segment(v, W.R, W.L, W.alpha, metric=W.metric) for v in vd]
     torch.cuda.synchronize()
@@ -418,12 +459,12 @@ def run_ours(args, ws, rank, local):
         prec = {"bf16": rn.BF16, "fp8": rn.FP8}[name]
         pq = rn.params(W.R, W.L, W.alpha, metric=W.metric, prec=prec)
         oq = torch.empty_like(out)
-        for _ in range(2):
+        for _ in range(1 if huge else 2):
             rn.merge(tsegs, pq, plan=plan_now(), out=oq)
         torch.cuda.synchronize()
         q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         qs = []
-        nq = max(3, args.steps // 2)
+        nq = 1 if huge else max(3, args.steps // 2)
         q0.record(stream)
         for _ in range(nq):
             _, st = rn.merge(tsegs, pq, plan=plan_now(), out=oq)
@@ -442,7 +483,7 @@ def run_ours(args, ws, rank, local):
                            "samples": int(qs[-1]["tile_error"][3])},
                        "prune_ms": round(sum(st["phase_ms"][6] + st["phase_ms"][7]
                                              for st in qs) / nq, 3)}
-    if W.multi:
+    if W.multi and not huge:   # (a plan of many groups runs eagerly anyway)
         # batching pattern: S4..S7 of the plan captured once in a CUDA graph, replayed
         pg = rn.params(W.R, W.L, W.alpha, metric=W.metric, flags=rn.FLAG_GRAPH)
         og = torch.empty_like(out)
@@ -473,8 +514,9 @@ def run_ours(args, ws, rank, local):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier(dist)
     torch.cuda.synchronize()
+    e2e_steps = 1 if huge else args.steps
     e0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(e2e_steps):
         for a, b in zip(dv, pin_v):
             a.copy_(b, non_blocking=True)
         for a, b in zip(dg, pin_g):
@@ -485,12 +527,12 @@ def run_ours(args, ws, rank, local):
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = allmax(dist, e0.elapsed_time(e1))
-    e2e = {"value": whole_job_rate(N, args.steps, ws, e2e_ms), "unit": UNIT,
+    e2e = {"value": whole_job_rate(N, e2e_steps, ws, e2e_ms), "unit": UNIT,
            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
     rec = None
     if rank == 0 and args.recall_queries > 0:
-        Xd = torch.cat(vd)
+        Xd = concat_rows(torch, vd)
         big = int(np.argmax(sizes))
         entry = graphs[big][1] + sum(sizes[:big])
         rec = {"ef": 64, "queries": args.recall_queries,

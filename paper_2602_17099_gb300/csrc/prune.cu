@@ -779,7 +779,8 @@ cudaError_t launch_small(const PruneArgs &a, cudaStream_t st) {
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, prune_small_kernel, kSmallThreads, 0);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
-    const int chunk = a.skip_empty_csr ? 32 : 1;
+    // owners are claimed a few at a time: one atomic round trip per claim
+    const int chunk = a.skip_empty_csr ? 32 : 4;
     int64_t grid = (int64_t)sms * per_sm;
     const int64_t want = (a.n_owners + chunk - 1) / chunk;
     if (want < grid) grid = want;

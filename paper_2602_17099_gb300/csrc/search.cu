@@ -41,14 +41,16 @@ SearchArgs subrange(const SearchArgs &a, int64_t q0, int64_t q1) {
 }
 
 // Autotuner: the first launch with at least kTuneMin queries for a (dim,
-// beam) shape runs every variant on slices of its queries: one untimed
-// warm-up slice each, then two timed slices each in alternating order (CUDA
-// events on the launching stream); the variant with the smallest time per
-// slice is kept for later launches.  Every variant computes the same results,
-// so the choice never changes them.
+// beam) shape runs every variant on the same slices of its queries: one
+// untimed warm-up slice, then kTuneReps timed slices, each run by every
+// variant in turn (order alternating between slices; CUDA events on the
+// launching stream).  The variant with the smallest total time is kept for
+// later launches.  Every variant computes the same results, so running a
+// slice again only costs time, and the comparison is on identical work.
 constexpr int64_t kTuneWarm = 2000;
-constexpr int64_t kTuneSlice = 10000;
-constexpr int64_t kTuneMin = kVariants * (kTuneWarm + 2 * kTuneSlice) + 10000;
+constexpr int64_t kTuneSlice = 8000;
+constexpr int kTuneReps = 3;
+constexpr int64_t kTuneMin = kTuneWarm + kTuneReps * kTuneSlice + 10000;
 std::mutex g_tune_mu;
 std::map<std::pair<int, int>, int> g_tuned;
 
@@ -86,9 +88,9 @@ cudaError_t launch_search(const SearchArgs &a, cudaStream_t st) {
         if (it != g_tuned.end()) var = it->second;
     }
     if (var >= 0 || a.nq < kTuneMin) return launch_dim_any(a, var >= 0 ? var : 0, st);
-    // slices of the batch run in turn; their results are final
-    float best_ms[kVariants];
-    for (int v = 0; v < kVariants; ++v) best_ms[v] = 3.4e38f;
+    // every variant runs each slice; the slices' results are final
+    float total_ms[kVariants];
+    for (int v = 0; v < kVariants; ++v) total_ms[v] = 0.f;
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return launch_dim_any(a, 0, st);
@@ -96,8 +98,7 @@ cudaError_t launch_search(const SearchArgs &a, cudaStream_t st) {
     int64_t pos = 0;
     auto run_slice = [&](int v, int64_t len, bool timed) {
         const SearchArgs sl = subrange(a, pos, pos + len);
-        pos += len;
-        err = cudaMemsetAsync(a.work, 0, sizeof(int32_t), st);  // each slice starts its own count
+        err = cudaMemsetAsync(a.work, 0, sizeof(int32_t), st);  // each run starts its own count
         if (err != cudaSuccess) return;
         if (timed) cudaEventRecord(e0, st);
         err = launch_dim_any(sl, v, st);
@@ -106,18 +107,21 @@ cudaError_t launch_search(const SearchArgs &a, cudaStream_t st) {
         err = cudaEventSynchronize(e1);
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < best_ms[v]) best_ms[v] = ms;
+        total_ms[v] += ms;
     };
     for (int v = 0; v < kVariants && err == cudaSuccess; ++v) run_slice(v, kTuneWarm, false);
-    for (int rep = 0; rep < 2 && err == cudaSuccess; ++rep)
+    pos += kTuneWarm;
+    for (int rep = 0; rep < kTuneReps && err == cudaSuccess; ++rep) {
         for (int k = 0; k < kVariants && err == cudaSuccess; ++k)
-            run_slice(rep == 0 ? k : kVariants - 1 - k, kTuneSlice, true);
+            run_slice(rep % 2 == 0 ? k : kVariants - 1 - k, kTuneSlice, true);
+        pos += kTuneSlice;
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (err != cudaSuccess) return err;
     int best = 0;
     for (int v = 1; v < kVariants; ++v)
-        if (best_ms[v] < best_ms[best]) best = v;
+        if (total_ms[v] < total_ms[best]) best = v;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         g_tuned[key] = best;

@@ -27,6 +27,7 @@ __all__ = [
     "gaussian",
     "sift_like",
     "deep_like",
+    "deep_like_gpu_segments",
     "embed_like",
     "random_partition",
     "cluster_partition",
@@ -114,6 +115,60 @@ def deep_like(n: int, seed: int, d: int = 96, n_comp: int = 1000, rank: int = 32
     return out
 
 
+def deep_like_gpu_segments(n: int, nq: int, seed: int, sizes, part_seed: int, device="cuda",
+                           d: int = 96, n_comp: int = 1000, rank: int = 32, scale: float = 0.06,
+                           noise: float = 0.01, chunk: int = 1 << 15):
+    """The DEEP stand-in's recipe (deep_like) drawn with a seeded torch
+    generator on `device`, for workloads of tens of GB: the same mixture and
+    parameters, other random numbers.  Rows 0..n-1 are cluster-partitioned as
+    in cluster_partition (components sorted by a random projection of their
+    means, assigned contiguously to segments of the given sizes) and written in
+    partition order into one tensor; the segments are views of it (rows in
+    ascending order within a segment).  Returns (segments, queries)."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    f32 = dict(device=device, dtype=torch.float32)
+
+    def normalise(x):
+        return x / x.norm(dim=1, keepdim=True).clamp_min(1e-30)
+
+    means = normalise(torch.randn(n_comp, d, generator=g, **f32))
+    A = torch.randn(n_comp, d, rank, generator=g, **f32) * scale
+    comp = torch.randint(0, n_comp, (n + nq,), generator=g, device=device)
+    gp = torch.Generator(device=device)
+    gp.manual_seed(part_seed)
+    proj = means @ torch.randn(d, generator=gp, **f32)
+    comp_rank = torch.empty(n_comp, dtype=torch.int64, device=device)
+    comp_rank[torch.argsort(proj, stable=True)] = torch.arange(n_comp, device=device)
+    order = torch.argsort(comp_rank[comp[:n]], stable=True)   # ties by row id
+    sizes_t = torch.as_tensor(np.asarray(sizes, dtype=np.int64), device=device)
+    bounds = torch.cat([torch.zeros(1, dtype=torch.int64, device=device), torch.cumsum(sizes_t, 0)])
+    # destination of every row: its segment's start + its rank among that segment's rows
+    dest = torch.empty(n, dtype=torch.int64, device=device)
+    for k in range(len(sizes)):
+        rows = torch.sort(order[bounds[k]:bounds[k + 1]]).values
+        dest[rows] = bounds[k] + torch.arange(rows.numel(), device=device)
+    del order
+    allx = torch.empty((n, d), **f32)
+    Q = torch.empty((nq, d), **f32)
+    for s in range(0, n + nq, chunk):
+        e = min(n + nq, s + chunk)
+        c = comp[s:e]
+        z = torch.randn(e - s, rank, generator=g, **f32)
+        x = means[c] + noise * torch.randn(e - s, d, generator=g, **f32)
+        x += torch.bmm(A[c], z.unsqueeze(2)).squeeze(2)
+        x = normalise(x)
+        e0 = min(e, n)
+        if s < e0:
+            allx[dest[s:e0]] = x[:e0 - s]
+        if e > n:
+            lo = max(s, n)
+            Q[lo - n:e - n] = x[lo - s:]
+    segs = [allx[int(bounds[k]):int(bounds[k + 1])] for k in range(len(sizes))]
+    return segs, Q
+
+
 def embed_like(n: int, seed: int, d: int = 768, n_comp: int = 2000,
                rank: int = 32, noise: float = 0.013) -> np.ndarray:
     """Unit-norm anisotropic mixture: x = normalise(mu_j + A_j z + noise*eps),
@@ -151,16 +206,21 @@ def lognormal_sizes(m: int, total: int, lo: int, hi: int, seed: int,
     g = _rng(seed)
     w = g.lognormal(0.0, sigma, size=m)
     sizes = np.clip(np.rint(w / w.sum() * total), lo, hi).astype(np.int64)
-    # Spread the rounding/clipping remainder over unclipped segments.
+    # Spread the rounding / clipping remainder evenly over the segments that can
+    # still move in its direction (lowest indices take the odd rows), until the
+    # sizes sum to `total` or every segment sits at its bound.
     diff = int(total - sizes.sum())
-    i = 0
-    while diff != 0 and i < 100 * m:
-        j = i % m
-        step = 1 if diff > 0 else -1
-        if lo <= sizes[j] + step <= hi:
-            sizes[j] += step
-            diff -= step
-        i += 1
+    while diff != 0:
+        free = [j for j in range(m) if (sizes[j] < hi if diff > 0 else sizes[j] > lo)]
+        if not free:
+            break
+        q, r = divmod(abs(diff), len(free))
+        for idx, j in enumerate(free):
+            want = q + (1 if idx < r else 0)
+            room = (hi - sizes[j]) if diff > 0 else (sizes[j] - lo)
+            step = min(want, int(room))
+            sizes[j] += step if diff > 0 else -step
+        diff = int(total - sizes.sum())
     return sizes
 
 
