@@ -351,6 +351,31 @@ def concat_rows(torch, vd):
     return vd[0].as_strided((off, d), (d, 1))
 
 
+def e2e_room(torch, in_bytes, out_bytes):
+    """None if host and device hold a pinned copy of the inputs and outputs and a
+    second device copy of the inputs with room to spare, else the reason."""
+    avail = None
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemAvailable:"):
+                    avail = int(line.split()[1]) * 1024
+    except OSError:
+        pass
+    need_host = in_bytes + out_bytes
+    if avail is not None and avail < 2 * need_host + (16 << 30):
+        return f"host memory: {avail >> 30} GiB available, {need_host >> 30} GiB to pin"
+    free, _ = torch.cuda.mem_get_info()
+    if free < 1.1 * in_bytes + (4 << 30):
+        return f"device memory: {free >> 30} GiB free, {in_bytes >> 30} GiB of inputs to copy"
+    return None
+
+
+def progress(msg):
+    """Progress on stderr (the JSON line stays alone on stdout)."""
+    print(f"[bench {time.strftime('%H:%M:%S')}] {msg}", file=sys.stderr, flush=True)
+
+
 def run_ours(args, ws, rank, local):
     import torch
 
@@ -375,10 +400,12 @@ def run_ours(args, ws, rank, local):
     cen = centroids_of(segs)
     vd = [s_ if torch.is_tensor(s_) else torch.from_numpy(s_).cuda() for s_ in segs]
     huge = N > 20_000_000   # tens of GB: fewer repetitions of the extra measurements
+    progress(f"{W.name}: {len(vd)} segments, {N} rows on the device")
     t0 = time.perf_counter()
     graphs = [rn.build_segment(v, W.R, W.L, W.alpha, metric=W.metric) for v in vd]
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
+    progress(f"input graphs built in {build_s:.1f} s")
     tsegs = [(v, g, e) for v, (g, e) in zip(vd, graphs)]
     sizes = [len(s_) for s_ in segs]
 
@@ -418,6 +445,7 @@ def run_ours(args, ws, rank, local):
     ms_max = allmax(dist, ms)
     value = whole_job_rate(N, args.steps, ws, ms_max)
 
+    progress(f"timed steps: {ms / args.steps:.1f} ms per step")
     # roofline of the search kernel (S1, S4, S5 launches), from the
     # library's CUDA events on the launching stream and its NDC counters
     s_bytes = s_ms = 0.0
@@ -503,33 +531,42 @@ def run_ours(args, ws, rank, local):
     modes["fp32"] = {"ms_per_step": ms_max / args.steps,
                      "prune_ms": round(phase_ms["S6_source_prune"] + phase_ms["S7_reverse_edges"], 3)}
 
+    progress("precision modes done")
     # end to end through the public API with host buffers
-    pin_v = [s_.cpu().pin_memory() for s_ in vd]
-    pin_g = [g.cpu().pin_memory() for g, _ in graphs]
-    pin_out = torch.empty((N, W.R), dtype=torch.int32).pin_memory()
-    dv = [torch.empty_like(v) for v in vd]
-    dg = [torch.empty_like(g) for g, _ in graphs]
-    h2d = sum(t.numel() * t.element_size() for t in pin_v + pin_g)
-    d2h = pin_out.numel() * pin_out.element_size()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    barrier(dist)
-    torch.cuda.synchronize()
-    e2e_steps = 1 if huge else args.steps
-    e0.record(stream)
-    for _ in range(e2e_steps):
-        for a, b in zip(dv, pin_v):
-            a.copy_(b, non_blocking=True)
-        for a, b in zip(dg, pin_g):
-            a.copy_(b, non_blocking=True)
-        rn.merge([(v, g, e) for v, g, (_, e) in zip(dv, dg, graphs)], p, plan=plan_now(),
-                 out=out)
-        pin_out.copy_(out, non_blocking=True)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = allmax(dist, e0.elapsed_time(e1))
-    e2e = {"value": whole_job_rate(N, e2e_steps, ws, e2e_ms), "unit": UNIT,
-           "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+    in_bytes = sum(v.numel() * 4 for v in vd) + sum(g.numel() * 4 for g, _ in graphs)
+    out_bytes = N * W.R * 4
+    room = e2e_room(torch, in_bytes, out_bytes)
+    if room is not None:
+        e2e = {"value": None, "unit": UNIT, "skipped": room}
+    else:
+        pin_v = [torch.empty(v.shape, dtype=v.dtype, pin_memory=True).copy_(v) for v in vd]
+        pin_g = [torch.empty(g.shape, dtype=g.dtype, pin_memory=True).copy_(g) for g, _ in graphs]
+        pin_out = torch.empty((N, W.R), dtype=torch.int32).pin_memory()
+        dv = [torch.empty_like(v) for v in vd]
+        dg = [torch.empty_like(g) for g, _ in graphs]
+        h2d = sum(t.numel() * t.element_size() for t in pin_v + pin_g)
+        d2h = pin_out.numel() * pin_out.element_size()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier(dist)
+        torch.cuda.synchronize()
+        e2e_steps = 1 if huge else args.steps
+        e0.record(stream)
+        for _ in range(e2e_steps):
+            for a, b in zip(dv, pin_v):
+                a.copy_(b, non_blocking=True)
+            for a, b in zip(dg, pin_g):
+                a.copy_(b, non_blocking=True)
+            rn.merge([(v, g, e) for v, g, (_, e) in zip(dv, dg, graphs)], p, plan=plan_now(),
+                     out=out)
+            pin_out.copy_(out, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = allmax(dist, e0.elapsed_time(e1))
+        e2e = {"value": whole_job_rate(N, e2e_steps, ws, e2e_ms), "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+        del pin_v, pin_g, pin_out, dv, dg
 
+    progress(f"e2e: {e2e.get('value')}")
     rec = None
     if rank == 0 and args.recall_queries > 0:
         Xd = concat_rows(torch, vd)
