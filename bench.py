@@ -206,24 +206,55 @@ def host_plan(W, segs, planner):
     return planner([len(s_) for s_ in segs], centroids_of(segs))
 
 
-def oracle_sample(W, args):
+def oracle_sample(W, args, nq=10):
     """Bounded sample of the workload for the CPU oracle: the same recipe at
-    ``W.oracle_scale`` of the full size, graphs built by the oracle (untimed)."""
+    ``W.oracle_scale`` of the full size (and nq queries of the same draw),
+    graphs built by the oracle (untimed)."""
     import oracle
-    segs, _ = W.make(W.oracle_scale, 10)
+    segs, Q = W.make(W.oracle_scale, nq)
     segs = [to_host(s_) for s_ in segs]
     gs = [oracle.build_graph(s_, W.R, W.L, W.alpha, metric=W.metric) for s_ in segs]
-    return oracle, segs, gs
+    return oracle, segs, gs, to_host(Q)
 
 
-def oracle_merge_once(W, oracle, segs, gs):
-    t0 = time.perf_counter()
+def sample_plan(W, oracle, segs):
     plan = host_plan(W, segs, lambda sz, c: oracle.mos_plan(sz, c))
     if plan is None:
         plan = oracle.pair_plan([len(s_) for s_ in segs])
-    oracle.rnsm_merge(segs, [g for g, _ in gs], [e for _, e in gs],
-                      [(a, b) for a, b, *_ in plan], W.R, W.L, W.alpha, metric=W.metric)
+    return [(a, b) for a, b, *_ in plan]
+
+
+def oracle_merge_once(W, oracle, segs, gs, keep=None):
+    t0 = time.perf_counter()
+    plan = sample_plan(W, oracle, segs)
+    merged, _ = oracle.rnsm_merge(segs, [g for g, _ in gs], [e for _, e in gs], plan, W.R, W.L,
+                                  W.alpha, metric=W.metric)
+    if keep is not None:
+        keep["merged"] = merged
     return time.perf_counter() - t0
+
+
+def recall_parity(W, oracle, segs, gs, Q, merged_oracle, rn, torch, ef=64):
+    """Recall@10 of the oracle-merged and the GPU-merged graph of the same sample
+    (same input graphs, same plan), both searched by the oracle's Algorithm 1
+    from the largest segment's entry, against the FP64 brute force."""
+    plan = sample_plan(W, oracle, segs)
+    tsegs = [(torch.from_numpy(s_).cuda(), torch.from_numpy(g).cuda(), e) for s_, (g, e) in zip(segs, gs)]
+    merged_gpu, _ = rn.merge(tsegs, rn.params(W.R, W.L, W.alpha, metric=W.metric),
+                             plan=[(a, b, 0.0) for a, b in plan])
+    merged_gpu = merged_gpu.cpu().numpy()
+    X = np.concatenate(segs)
+    sizes = [len(s_) for s_ in segs]
+    big = int(np.argmax(sizes))
+    entry = gs[big][1] + sum(sizes[:big])
+    _, gd = oracle.bruteforce_knn(X, Q, 10, metric=W.metric)
+    seeds = np.full((len(Q), 1), entry, np.int32)
+    out = {"queries": len(Q), "ef": ef,
+           "identical_rows": float((merged_gpu == merged_oracle).all(axis=1).mean())}
+    for name, adj in (("oracle_merged", merged_oracle), ("gpu_merged", merged_gpu)):
+        ids = oracle.beam_search(X, adj, Q, seeds, ef, 10, metric=W.metric)[0]
+        out[name] = oracle.recall_at_k(ids, X, gd, Q, metric=W.metric)
+    return out
 
 
 def sample_desc(W, segs):
@@ -231,25 +262,29 @@ def sample_desc(W, segs):
             f"{sum(len(s_) for s_ in segs)} rows, FP64 C oracle with OpenMP")
 
 
-def cpu_baseline(W, args, min_s=10.0, max_runs=40):
+def cpu_baseline(W, args, min_s=10.0, max_runs=40, rn=None, torch=None):
     """The oracle's merge on the bounded sample, repeated until about min_s of CPU
-    time has been measured (the sample itself can take well under a second)."""
-    oracle, segs, gs = oracle_sample(W, args)
+    time has been measured (the sample itself can take well under a second).
+    With the library at hand, also the recall parity of the two merged graphs."""
+    oracle, segs, gs, Q = oracle_sample(W, args, nq=200)
     n = sum(len(s_) for s_ in segs)
-    total, runs = 0.0, 0
+    total, runs, keep = 0.0, 0, {}
     while runs < max_runs and (runs == 0 or total < min_s):
-        total += oracle_merge_once(W, oracle, segs, gs)
+        total += oracle_merge_once(W, oracle, segs, gs, keep)
         runs += 1
-    return {"value": n * runs / total, "unit": UNIT, "cores": oracle.max_threads(),
-            "kind": "oracle",
-            "sample": sample_desc(W, segs) + f", {runs} merges in {total:.2f} s"}
+    out = {"value": n * runs / total, "unit": UNIT, "cores": oracle.max_threads(),
+           "kind": "oracle",
+           "sample": sample_desc(W, segs) + f", {runs} merges in {total:.2f} s"}
+    if rn is not None:
+        out["recall_parity"] = recall_parity(W, oracle, segs, gs, Q, keep["merged"], rn, torch)
+    return out
 
 
 def run_reference(args, ws, rank):
     if rank != 0:
         return 0
     W = WORKLOADS[args.workload]
-    oracle, segs, gs = oracle_sample(W, args)
+    oracle, segs, gs, _ = oracle_sample(W, args)
     n = sum(len(s_) for s_ in segs)
     for _ in range(args.warmup):
         oracle_merge_once(W, oracle, segs, gs)
@@ -302,11 +337,13 @@ def recall_at_10(rn, torch, W, Xd, adj, entry, Q, ef=64, chunk_rows=1 << 22, qb=
     """Tie-tolerant Recall@10 of the merged graph (evaluation only): a returned
     id counts if its FP64 distance is within the true 10th-NN distance.  The
     true neighbours come from a chunked FP32 scan (top 32 per query) re-ranked
-    in FP64."""
+    in FP64.  entry: one global id, or a list (every query seeded with all)."""
     Qd = Q if torch.is_tensor(Q) else torch.from_numpy(Q)
     Qd = Qd.cuda()
     nq = Qd.shape[0]
-    seeds = torch.full((nq, 1), entry, dtype=torch.int32, device="cuda")
+    ent = torch.tensor(entry if isinstance(entry, (list, tuple)) else [entry], dtype=torch.int32,
+                       device="cuda")
+    seeds = ent[None, :].expand(nq, ent.numel()).contiguous()
     ids, _, _ = rn.search(Xd, adj, Qd, seeds, ef, 10, metric=W.metric)
 
     def native(rows64, q64):
@@ -574,10 +611,14 @@ def run_ours(args, ws, rank, local):
         entry = graphs[big][1] + sum(sizes[:big])
         rec = {"ef": 64, "queries": args.recall_queries,
                "value": recall_at_10(rn, torch, W, Xd, out, entry, Q)}
+        if W.multi:   # one entry per segment: cross-segment navigation taken out
+            offs = np.concatenate([[0], np.cumsum(sizes)])
+            rec["value_segment_entries"] = recall_at_10(
+                rn, torch, W, Xd, out, [int(graphs[k][1] + offs[k]) for k in range(len(sizes))], Q)
 
     base = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        base = cpu_baseline(W, args)
+        base = cpu_baseline(W, args, rn=rn, torch=torch)
 
     if rank == 0:
         vec_bytes = sum(v.numel() * 4 for v in vd)
