@@ -661,16 +661,32 @@ __global__ void __launch_bounds__(kSmallThreads, 3) prune_small_kernel(const Pru
                 kept = live;
                 nk = np;
             } else {
-                // the greedy walk (every lane runs it on the same values)
-                for (int c = 0; c < nr && nk < R; ++c) {
-                    if (!((live >> c) & 1ull)) continue;
-                    const unsigned long long oc = (unsigned long long)s.occ[2 * c] |
-                                                  ((unsigned long long)s.occ[2 * c + 1] << 32);
-                    if (!(oc & kept)) {
-                        kept |= 1ull << c;
-                        ++nk;
-                    }
+                // The greedy walk in rounds: a position is decided once every live
+                // occluder before it is; it is kept iff none of those is kept.  Each
+                // decision depends only on earlier positions, so this is the walk's
+                // uncapped kept set; the walk's cap keeps its first R positions.
+                // Lane l holds positions l and l + 32.
+                const unsigned long long oc0 =
+                    lane < nr ? ((unsigned long long)s.occ[2 * lane] |
+                                 ((unsigned long long)s.occ[2 * lane + 1] << 32)) & live : 0ull;
+                const unsigned long long oc1 =
+                    lane + 32 < nr ? ((unsigned long long)s.occ[2 * (lane + 32)] |
+                                      ((unsigned long long)s.occ[2 * (lane + 32) + 1] << 32)) & live
+                                   : 0ull;
+                const unsigned long long b0 = 1ull << lane, b1 = 1ull << (lane + 32);
+                unsigned long long decided = ~live, kall = 0ull;   // non-live: never kept
+                while (~decided) {
+                    const bool r0 = !(decided & b0) && !(oc0 & ~decided);
+                    const bool r1 = !(decided & b1) && !(oc1 & ~decided);
+                    const bool k0 = r0 && !(oc0 & kall), k1 = r1 && !(oc1 & kall);
+                    decided |= (unsigned long long)__ballot_sync(0xffffffffu, r0) |
+                               ((unsigned long long)__ballot_sync(0xffffffffu, r1) << 32);
+                    kall |= (unsigned long long)__ballot_sync(0xffffffffu, k0) |
+                            ((unsigned long long)__ballot_sync(0xffffffffu, k1) << 32);
                 }
+                while (__popcll(kall) > R) kall &= ~(1ull << (63 - __clzll((long long)kall)));
+                kept = kall;
+                nk = __popcll(kall);
             }
             int32_t *out = a.out + (a.out_by_index ? i : (int64_t)owner) * R;
             const bool k0 = (kept >> lane) & 1ull, k1 = (kept >> (lane + 32)) & 1ull;
