@@ -702,33 +702,60 @@ __global__ void __launch_bounds__(kThreads, 2) prune_tc_kernel(const PruneArgs a
             const int np = __popc(lv[0]) + __popc(lv[1]) + __popc(lv[2]) + __popc(lv[3]);
             int nk = 0;
             if (a.keep_all_if_fit && np <= R) {
-                for (int r = 0; r < nc; ++r) {
-                    const uint32_t lw = r < 32 ? lv[0] : r < 64 ? lv[1] : r < 96 ? lv[2] : lv[3];
-                    if ((lw >> (r & 31)) & 1u) {
-                        if (lane == 0) s.kept[nk] = s.pid[s.order[r]];
-                        ++nk;
-                    }
+                nk = np;
+                int before = 0;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    if ((lv[q] >> lane) & 1u)
+                        s.kept[before + __popc(lv[q] & lanemask_lt())] = s.pid[s.order[32 * q + lane]];
+                    before += __popc(lv[q]);
                 }
             } else {
-                uint32_t k0 = 0, k1 = 0, k2 = 0, k3 = 0;   // kept positions
-#pragma unroll 4
-                for (int r = 0; r < nc; ++r) {
-                    const uint4 oc = *reinterpret_cast<const uint4 *>(s.occp[r]);
-                    const uint32_t lw = r < 32 ? lv[0] : r < 64 ? lv[1] : r < 96 ? lv[2] : lv[3];
-                    const bool take = nk < R && ((lw >> (r & 31)) & 1u) &&
-                                      ((oc.x & k0) | (oc.y & k1) | (oc.z & k2) | (oc.w & k3)) == 0u;
-                    if (take) {
-                        const uint32_t bit = 1u << (r & 31);
-                        k0 |= r < 32 ? bit : 0u;
-                        k1 |= (r >> 5) == 1 ? bit : 0u;
-                        k2 |= (r >> 5) == 2 ? bit : 0u;
-                        k3 |= (r >> 5) == 3 ? bit : 0u;
-                        if (lane == 0) s.kept[nk] = r;   // positions; ids below
-                        ++nk;
+                // The greedy walk in ballot rounds (as the FP32 small-pool prune): a
+                // position is decided once every live occluder before it is, and kept
+                // iff none of those is kept; the cap keeps the first R kept positions.
+                // Lane l holds positions l, l + 32, l + 64 and l + 96.
+                uint32_t oc[4][4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const uint4 o = *reinterpret_cast<const uint4 *>(s.occp[32 * q + lane]);
+                    oc[q][0] = o.x & lv[0];
+                    oc[q][1] = o.y & lv[1];
+                    oc[q][2] = o.z & lv[2];
+                    oc[q][3] = o.w & lv[3];
+                }
+                uint32_t dec[4] = {~lv[0], ~lv[1], ~lv[2], ~lv[3]};   // non-live: never kept
+                uint32_t kall[4] = {0u, 0u, 0u, 0u};
+                while ((dec[0] & dec[1] & dec[2] & dec[3]) != 0xffffffffu) {
+                    bool r[4], k[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const bool und = ((oc[q][0] & ~dec[0]) | (oc[q][1] & ~dec[1]) |
+                                          (oc[q][2] & ~dec[2]) | (oc[q][3] & ~dec[3])) != 0u;
+                        r[q] = !((dec[q] >> lane) & 1u) && !und;
+                        k[q] = r[q] && ((oc[q][0] & kall[0]) | (oc[q][1] & kall[1]) |
+                                        (oc[q][2] & kall[2]) | (oc[q][3] & kall[3])) == 0u;
+                    }
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        dec[q] |= __ballot_sync(0xffffffffu, r[q]);
+                        kall[q] |= __ballot_sync(0xffffffffu, k[q]);
                     }
                 }
-                __syncwarp();
-                for (int j = lane; j < nk; j += 32) s.kept[j] = s.pid[s.order[s.kept[j]]];
+                int tot = __popc(kall[0]) + __popc(kall[1]) + __popc(kall[2]) + __popc(kall[3]);
+                for (int q = 3; q >= 0; --q)   // drop kept positions past the R-th
+                    while (tot > R && kall[q]) {
+                        kall[q] &= ~(1u << (31 - __clz(kall[q])));
+                        --tot;
+                    }
+                nk = tot;
+                int before = 0;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    if ((kall[q] >> lane) & 1u)
+                        s.kept[before + __popc(kall[q] & lanemask_lt())] = s.pid[s.order[32 * q + lane]];
+                    before += __popc(kall[q]);
+                }
             }
             __syncwarp();
             int32_t *out = a.out + (a.out_by_index ? i : (int64_t)owner) * R;
