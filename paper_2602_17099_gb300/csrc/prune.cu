@@ -487,7 +487,10 @@ struct SmallSmem {
     uint32_t occ[2 * kSmallMax];
 };
 
-__global__ void __launch_bounds__(kSmallThreads, 3) prune_small_kernel(const PruneArgs a, int chunk) {
+#ifndef RNSM_SMALL_MIN_BLOCKS
+#define RNSM_SMALL_MIN_BLOCKS 4   // resident CTAs per SM the register budget is cut for
+#endif
+__global__ void __launch_bounds__(kSmallThreads, RNSM_SMALL_MIN_BLOCKS) prune_small_kernel(const PruneArgs a, int chunk) {
     __shared__ __align__(16) SmallSmem s;
     __shared__ int64_t sh_i;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
