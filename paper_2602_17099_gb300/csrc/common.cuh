@@ -67,6 +67,10 @@ __device__ __forceinline__ int lower_bound_lex(const float *sd, const int32_t *s
     return lo;
 }
 
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 __device__ __forceinline__ float4 ldg4(const float *p) {
     return __ldg(reinterpret_cast<const float4 *>(p));
 }

@@ -649,6 +649,36 @@ __global__ void __launch_bounds__(kSmallThreads, RNSM_SMALL_MIN_BLOCKS) prune_sm
         }
         __syncthreads();
 
+        if (warp != 0 && i + 1 < i1) {
+            // while warp 0 walks, the other warps bring the next owner's rows into L2
+            const int64_t in = i + 1;
+            const int32_t on = a.owner_ids ? a.owner_ids[in] : (int32_t)(a.owner_base + in);
+            int64_t cl = 0, ch = 0;
+            if (a.csr_offs) {
+                cl = a.csr_offs[in];
+                ch = a.csr_offs[in + 1];
+            }
+            const int64_t nrn = (int64_t)a.lenA + a.lenB + (ch - cl);
+            if (nrn <= kSmallMax && !(a.skip_empty_csr && ch == cl)) {
+                for (int j = tid - 32; j <= nrn; j += kSmallThreads - 32) {
+                    int32_t id = on;   // j == nrn: the owner
+                    if (j < nrn) {
+                        if (j < a.lenA) {
+                            id = a.listA[(int64_t)on * a.lenA + j];
+                        } else if (j < a.lenA + a.lenB) {
+                            id = a.listB[in * a.strideB + (j - a.lenA)];
+                            if (id >= 0) id += a.offB;
+                        } else {
+                            id = a.csr_ids[cl + (j - a.lenA - a.lenB)];
+                        }
+                    }
+                    if (id < 0) continue;
+                    const char *row = reinterpret_cast<const char *>(seg_row(a.segs, id, dim));
+                    for (int l = 0; l < dim * 4; l += 128) prefetch_l2(row + l);
+                }
+            }
+        }
+
         if (warp == 0) {
             // live positions: valid and not a repeat of the previous id
             const bool a0 = lane < nr && s.sid[lane] != INT32_MAX &&
