@@ -709,9 +709,13 @@ __global__ void __launch_bounds__(kSmallThreads, RNSM_SMALL_MIN_BLOCKS) prune_sm
                 const unsigned long long b0 = 1ull << lane, b1 = 1ull << (lane + 32);
                 unsigned long long decided = ~live, kall = 0ull;   // non-live: never kept
                 while (~decided) {
-                    const bool r0 = !(decided & b0) && !(oc0 & ~decided);
-                    const bool r1 = !(decided & b1) && !(oc1 & ~decided);
-                    const bool k0 = r0 && !(oc0 & kall), k1 = r1 && !(oc1 & kall);
+                    // dropped as soon as one occluder is kept; kept once every occluder
+                    // is decided and none is kept
+                    const bool d0 = !(decided & b0), d1 = !(decided & b1);
+                    const bool k0 = d0 && !(oc0 & kall) && !(oc0 & ~decided);
+                    const bool k1 = d1 && !(oc1 & kall) && !(oc1 & ~decided);
+                    const bool r0 = k0 || (d0 && (oc0 & kall));
+                    const bool r1 = k1 || (d1 && (oc1 & kall));
                     decided |= (unsigned long long)__ballot_sync(0xffffffffu, r0) |
                                ((unsigned long long)__ballot_sync(0xffffffffu, r1) << 32);
                     kall |= (unsigned long long)__ballot_sync(0xffffffffu, k0) |

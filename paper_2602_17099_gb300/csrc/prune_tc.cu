@@ -730,11 +730,15 @@ __global__ void __launch_bounds__(kThreads, 2) prune_tc_kernel(const PruneArgs a
                     bool r[4], k[4];
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
+                        // dropped as soon as one occluder is kept; kept once every
+                        // occluder is decided and none is kept
                         const bool und = ((oc[q][0] & ~dec[0]) | (oc[q][1] & ~dec[1]) |
                                           (oc[q][2] & ~dec[2]) | (oc[q][3] & ~dec[3])) != 0u;
-                        r[q] = !((dec[q] >> lane) & 1u) && !und;
-                        k[q] = r[q] && ((oc[q][0] & kall[0]) | (oc[q][1] & kall[1]) |
-                                        (oc[q][2] & kall[2]) | (oc[q][3] & kall[3])) == 0u;
+                        const bool hit = ((oc[q][0] & kall[0]) | (oc[q][1] & kall[1]) |
+                                          (oc[q][2] & kall[2]) | (oc[q][3] & kall[3])) != 0u;
+                        const bool open = !((dec[q] >> lane) & 1u);
+                        k[q] = open && !hit && !und;
+                        r[q] = k[q] || (open && hit);
                     }
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
