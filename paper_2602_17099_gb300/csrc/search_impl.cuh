@@ -73,7 +73,8 @@ __device__ __forceinline__ bool hash_insert(int32_t *hash, int H, int32_t id, bo
 template <int F4, int EFMAX, int VAR>
 __device__ __forceinline__ void process(const SearchArgs &a, const float *base, WarpSmem &w, int hslots,
                                         const float4 (&q)[Layout<F4>::V], int32_t c0, int32_t c1,
-                                        int &size, bool &overflow, unsigned long long &ndc) {
+                                        int &size, bool &overflow, unsigned long long &ndc,
+                                        int32_t pf = -1) {
     using Lay = Layout<F4, Variant<VAR>::kUMul2>;
     constexpr int G = Lay::G, V = Lay::V, RPI = Lay::RPI, U = Lay::U;
     const int lane = threadIdx.x & 31;
@@ -90,6 +91,13 @@ __device__ __forceinline__ void process(const SearchArgs &a, const float *base, 
     const int c = cnt0 + __popc(m1);
     if (n0) w.ci[__popc(m0 & lanemask_lt())] = c0;
     if (n1) w.ci[cnt0 + __popc(m1 & lanemask_lt())] = c1;
+    // pf: a neighbour of the entry likely to be expanded next; its row is brought
+    // into L2 now so that the next expansion's gather finds it there (a hint only)
+    if (pf >= 0) {
+        const char *pr = reinterpret_cast<const char *>(base + (int64_t)pf * (4 * F4));
+#pragma unroll
+        for (int l = 0; l < 16 * F4; l += 128) prefetch_l2(pr + l);
+    }
     __syncwarp();
     if (c == 0) return;
     ndc += (unsigned long long)c;
@@ -287,25 +295,35 @@ search_kernel(const SearchArgs a, int hslots) {
 
         // Expansion loop: nearest unexpanded entry first.
         for (;;) {
-            int found = -1;
-            for (int b = 0; b < size; b += 32) {
+            // the nearest unexpanded entry and the runner-up (usually expanded next)
+            int found = -1, second = -1;
+            for (int b = 0; b < size && second < 0; b += 32) {
                 const int i = b + lane;
                 const bool un = i < size && w.bi[i] >= 0;
-                const unsigned m = __ballot_sync(0xffffffffu, un);
-                if (m) { found = b + __ffs(m) - 1; break; }
+                unsigned m = __ballot_sync(0xffffffffu, un);
+                if (found < 0 && m) {
+                    found = b + __ffs(m) - 1;
+                    m &= m - 1u;
+                }
+                if (found >= 0 && m) second = b + __ffs(m) - 1;
             }
             if (found < 0) break;
             const int32_t u = w.bi[found];
+            const int r_in = JF(r_in);
+            const int32_t *adj = JF(adj);
+            // one neighbour of the runner-up per lane, to prefetch during this expansion
+            int32_t pf = -1;
+            if (second >= 0 && lane < r_in) pf = adj[(int64_t)(w.bi[second] & kIdMask) * r_in + lane];
             __syncwarp();
             if (lane == 0) w.bi[found] = u | kExpandedBit;
             __syncwarp();
             ++nexp;
-            const int r_in = JF(r_in);
-            const int32_t *nb = JF(adj) + (int64_t)u * r_in;
+            const int32_t *nb = adj + (int64_t)u * r_in;
             for (int j0 = 0; j0 < r_in; j0 += 64) {
                 const int32_t c0 = j0 + lane < r_in ? nb[j0 + lane] : -1;
                 const int32_t c1 = j0 + 32 + lane < r_in ? nb[j0 + 32 + lane] : -1;
-                process<F4, EFMAX, VAR>(a, base, w, hslots, q, c0, c1, size, overflow, ndc);
+                process<F4, EFMAX, VAR>(a, base, w, hslots, q, c0, c1, size, overflow, ndc,
+                                        j0 == 0 ? pf : -1);
             }
         }
 
