@@ -64,13 +64,9 @@ int search_variant_for(int dim, int ef) {
     return it == g_tuned.end() ? -1 : it->second;
 }
 
-namespace {
-
-}  // namespace
-
 bool search_would_tune(int dim, int ef, int64_t nq) {
     const char *force = getenv("RNSM_SEARCH_VARIANT");
-    if (force && (force[0] == '0' || force[0] == '1')) return false;
+    if (force && force[0] >= '0' && force[0] < '0' + kVariants) return false;
     if (nq < kTuneMin) return false;
     return search_variant_for(dim, ef) < 0;
 }
@@ -79,7 +75,7 @@ cudaError_t launch_search(const SearchArgs &a, cudaStream_t st) {
     if (a.nq <= 0) return cudaSuccess;
     if (!search_dim_supported(a.dim)) return cudaErrorInvalidValue;
     const char *force = getenv("RNSM_SEARCH_VARIANT");
-    if (force && (force[0] == '0' || force[0] == '1')) return launch_dim_any(a, force[0] - '0', st);
+    if (force && force[0] >= '0' && force[0] < '0' + kVariants) return launch_dim_any(a, force[0] - '0', st);
     const std::pair<int, int> key{a.dim, efmax_of(a.ef)};
     int var = -1;
     {

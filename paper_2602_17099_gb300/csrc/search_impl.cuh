@@ -36,12 +36,14 @@ __host__ __device__ constexpr size_t warp_smem_bytes(int efmax, int hslots) {
 
 // Launch-shape variants (identical results): 0 = half the rows in flight and
 // registers capped for 8 CTAs per SM; 1 = the full rows in flight, 5 CTAs.
+// A tuned variant number v selects shape v & 1 and, if v & 2, the L2
+// prefetch of the runner-up's neighbourhood during each expansion.
 template <int VAR>
 struct Variant {
     static constexpr int kUMul2 = VAR == 0 ? 1 : 2;  // rows in flight, in halves of U0
     static constexpr int kMinBlocks = VAR == 0 ? 8 : 5;
 };
-constexpr int kVariants = 2;
+constexpr int kVariants = 4;
 
 template <int F4, int UMUL2 = 2>
 struct Layout {
@@ -214,7 +216,7 @@ __device__ __forceinline__ void process(const SearchArgs &a, const float *base, 
 
 template <int F4, int EFMAX, int VAR, bool JOBS>
 __global__ void __launch_bounds__(kSearchWarps * 32, Variant<VAR>::kMinBlocks)
-search_kernel(const SearchArgs a, int hslots) {
+search_kernel(const SearchArgs a, int hslots, int prefetch) {
     using Lay = Layout<F4>;
     constexpr int G = Lay::G, V = Lay::V;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -297,7 +299,7 @@ search_kernel(const SearchArgs a, int hslots) {
         for (;;) {
             // the nearest unexpanded entry and the runner-up (usually expanded next)
             int found = -1, second = -1;
-            for (int b = 0; b < size && second < 0; b += 32) {
+            for (int b = 0; b < size && (prefetch ? second < 0 : found < 0); b += 32) {
                 const int i = b + lane;
                 const bool un = i < size && w.bi[i] >= 0;
                 unsigned m = __ballot_sync(0xffffffffu, un);
@@ -313,7 +315,7 @@ search_kernel(const SearchArgs a, int hslots) {
             const int32_t *adj = JF(adj);
             // one neighbour of the runner-up per lane, to prefetch during this expansion
             int32_t pf = -1;
-            if (second >= 0 && lane < r_in) pf = adj[(int64_t)(w.bi[second] & kIdMask) * r_in + lane];
+            if (prefetch && second >= 0 && lane < r_in) pf = adj[(int64_t)(w.bi[second] & kIdMask) * r_in + lane];
             __syncwarp();
             if (lane == 0) w.bi[found] = u | kExpandedBit;
             __syncwarp();
@@ -372,7 +374,7 @@ int hslots_for(int ef) {
 }
 
 template <int F4, int EFMAX, int VAR, bool JOBS>
-cudaError_t launch_t(const SearchArgs &a, cudaStream_t st) {
+cudaError_t launch_t(const SearchArgs &a, int prefetch, cudaStream_t st) {
     const int hslots = hslots_for(a.ef);
     const size_t smem = (size_t)kSearchWarps * warp_smem_bytes(EFMAX, hslots);
     auto kern = search_kernel<F4, EFMAX, VAR, JOBS>;
@@ -397,14 +399,15 @@ cudaError_t launch_t(const SearchArgs &a, cudaStream_t st) {
     int64_t want = (a.nq + kSearchWarps - 1) / kSearchWarps;
     int64_t grid = (int64_t)sms * per_sm;
     if (want < grid) grid = want < 1 ? 1 : want;
-    kern<<<(unsigned)grid, kSearchWarps * 32, smem, st>>>(a, hslots);
+    kern<<<(unsigned)grid, kSearchWarps * 32, smem, st>>>(a, hslots, prefetch);
     note_launches(1);
     return cudaGetLastError();
 }
 
 template <int F4, int EFMAX, bool JOBS>
 cudaError_t launch_var(const SearchArgs &a, int var, cudaStream_t st) {
-    return var == 0 ? launch_t<F4, EFMAX, 0, JOBS>(a, st) : launch_t<F4, EFMAX, 1, JOBS>(a, st);
+    const int pf = (var >> 1) & 1;
+    return (var & 1) == 0 ? launch_t<F4, EFMAX, 0, JOBS>(a, pf, st) : launch_t<F4, EFMAX, 1, JOBS>(a, pf, st);
 }
 
 template <int F4, bool JOBS>

@@ -441,14 +441,15 @@ def test_low_precision_merge_equals_fp32_embedding_shape(rn, prec):
 
 def test_search_variants_and_autotuned_launch_agree(rn, monkeypatch):
     # 60k queries trigger the autotuner (slices run with different launch
-    # shapes); every variant must give the same results as the oracle.
+    # shapes, with and without the L2 prefetch); every variant must give the
+    # same results as the oracle.
     X = gen.sift_like(20000, 101, d=32)
     adj, ep = oracle.build_graph(X, 16, 32, 1.2)
     Q = gen.sift_like(60000, 102, d=32)
     seeds = np.full((len(Q), 1), ep, np.int32)
     want, _, _, _, _ = oracle.beam_search(X, adj, Q, seeds, 24, 10)
     outs = []
-    for force in ("0", "1", None):
+    for force in ("0", "1", "2", "3", None):
         if force is None:
             monkeypatch.delenv("RNSM_SEARCH_VARIANT", raising=False)
         else:
