@@ -93,7 +93,7 @@ WORKLOADS = {
                            1.2, L2_METRIC, _sift, False, ("bf16", "fp8"), 0.1),
     "deep10x2m": Workload("deep10x2m", "deep-like 10 segments (lognormal 50k-400k, 2M total, "
                           "cluster partition) d96 L2 R32 L64 alpha1.2, MOS plan", 96, 32, 64,
-                          1.2, L2_METRIC, _deep, True, (), 0.02),
+                          1.2, L2_METRIC, _deep, True, ("bf16",), 0.02),
     "embed4x250k": Workload("embed4x250k", "embedding-like 4x250k d768 IP R64 L128 alpha1.2, "
                             "MOS plan", 768, 64, 128, 1.2, IP_METRIC, _embed, True,
                             ("bf16", "fp8"), 0.01),

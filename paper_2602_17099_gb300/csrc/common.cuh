@@ -84,6 +84,14 @@ __device__ __forceinline__ float4 ldg4(const float *p) {
 // packed f32x2 instruction, whose lanes round exactly as the scalar ones.
 typedef unsigned long long f2_t;
 
+__device__ __forceinline__ f2_t f2_of(float lo, float hi) {
+    f2_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void f2_split(f2_t a, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a));
+}
 __device__ __forceinline__ f2_t f2_sub(f2_t a, f2_t b) {
     f2_t r;
     asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));

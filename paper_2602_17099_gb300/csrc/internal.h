@@ -134,7 +134,14 @@ cudaError_t launch_prune(const PruneArgs &a, cudaStream_t st);
 // qnorm), 2 if it stages the FP32 rows split into two BF16 terms.
 int prune_tc_terms(int dim, int prec);
 int prune_tc_max_pool();
-cudaError_t launch_prune_tc(const PruneArgs &a, cudaStream_t st);
+cudaError_t launch_prune_tc(const PruneArgs &a, cudaStream_t st, int terms = 0);  // 0: prune_tc_terms
+// BF16 tensor-core prune of small pools, two owners per tile (L2, dim a
+// multiple of 16 up to 128, pools of up to prune_pair_max_pool() raw
+// candidates; FP32 rows centred and split into hi / lo terms in the kernel,
+// nothing stored).
+bool prune_pair_ok(int dim, int prec, int metric);
+int prune_pair_max_pool();
+cudaError_t launch_prune_pair(const PruneArgs &a, cudaStream_t st);
 // Rows of the segment table to BF16 (prec 1) or E4M3 with per-row scale (prec 2),
 // plus residual norms and row norms.
 // With q_lo (BF16 only) the rows are split into q = bf16(x) and q_lo = bf16(x - q)

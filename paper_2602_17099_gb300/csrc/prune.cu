@@ -805,14 +805,18 @@ cudaError_t launch_small(const PruneArgs &a, cudaStream_t st);
 cudaError_t launch_prune(const PruneArgs &a, cudaStream_t st) {
     if (a.n_owners <= 0) return cudaSuccess;
     if (a.R > 64 || a.dim > 1024 || (a.dim & 3)) return cudaErrorInvalidValue;
-    const int terms = a.prec != 0 ? prune_tc_terms(a.dim, a.prec) : 0;
+    // BF16 at small L2 dimensions: the pair tile; pools too large for it take the
+    // general tile with the FP32 rows split into two terms (no stored copies)
+    const bool pair_ok = a.prec != 0 && prune_pair_ok(a.dim, a.prec, a.metric);
+    const bool pair = pair_ok && a.lenA + a.lenB <= prune_pair_max_pool();
+    const int terms = pair ? 0 : pair_ok ? 2 : a.prec != 0 ? prune_tc_terms(a.dim, a.prec) : 0;
     const bool tc = terms == 2 || (terms == 1 && a.qrows);
-    const int cap = tc ? prune_tc_max_pool() : kSmallMax;   // pool of the first kernel
+    const int cap = pair ? prune_pair_max_pool() : tc ? prune_tc_max_pool() : kSmallMax;
     const bool small_ok = a.ovf_list && a.ovf_count && a.work2 && a.lenA + a.lenB <= cap;
     if (!small_ok) return launch_general(a, nullptr, nullptr, st);
     cudaError_t e = cudaMemsetAsync(a.ovf_count, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
-    e = tc ? launch_prune_tc(a, st) : launch_small(a, st);
+    e = pair ? launch_prune_pair(a, st) : tc ? launch_prune_tc(a, st, terms) : launch_small(a, st);
     if (e != cudaSuccess) return e;
     if (a.lenA + a.lenB + (a.csr_offs ? a.csr_max : 0) <= cap) return cudaSuccess;
     // owners whose pools exceeded the first kernel (the count stays on the device)

@@ -1,0 +1,520 @@
+// K4b: the BF16 tensor-core prune for small pools (L2, at most 64 raw
+// candidates, dimension a multiple of 16 up to 128), two owners per tile.
+//
+// The general tensor-core prune (prune_tc.cu) gives one CTA of eight warps to
+// one owner and spends most of its time in barrier-separated phases; for pools
+// of 64 candidates at d <= 128 the FP32 small-pool kernel was faster.  This
+// kernel packs two owners into one 128 x 128 Gram tile and keeps every phase
+// inside the two warps that own the candidates' TMEM lanes:
+//
+//  1. Owner distances, exact.  Each thread takes one pool slot and computes
+//     d(v, c) with the FP32 prune distance (the two-chain definition of
+//     common.cuh), so the (distance, id) order is the FP32 order without any
+//     interval logic; the slots are ranked by counting.
+//  2. Staging, in that order.  The thread of position p reads its candidate's
+//     FP32 row again, centres it on the owner (y = x_c - x_v, rounded once),
+//     splits y into hi = bf16(y) and lo = bf16(y - hi) and writes both into
+//     the K-major no-swizzle tile: rows 0..63 are owner A's positions, rows
+//     64..127 owner B's.  If every lo of the pair is zero (integer-valued
+//     data), only hi is used.
+//  3. One thread issues the MMAs (hi.hi, plus lo.hi, hi.lo and lo.lo) of the
+//     tile against itself, M = N = 128, into 128 TMEM columns, and commits
+//     them to an mbarrier (every wait bounded by 1 s).
+//  4. Warp w reads TMEM lanes 32w..32w+31, i.e. 32 positions s of one owner,
+//     and that owner's 64 columns c.  From the centred Gram G:
+//     d~(s, c) = G_ss + G_cc - 2 G_sc, with |d~ - d_fp32(s, c)| <=
+//     kappa (n_s + n_c)^2 <= b_s + b_c, n_r^2 a bound on the squared norm of
+//     the staged row r (from G_rr).  A test "s occludes c" (s before c) is
+//     settled by the tile when alpha (d~ +- (b_s + b_c)) - d(v, c) has one
+//     sign, else by a tighter per-pair bound, else by the exact FP32
+//     distance with the FP32 prune's own rule fmaf(alpha, d, -d(v, c)) <= 0.
+//     The ballots of a column are the occluder bits of c by position.
+//  5. One warp per owner runs the greedy walk in ballot rounds (as the FP32
+//     small-pool kernel) and writes the kept ids.
+//
+// The result equals the FP32 prune's: the order is exact, and every
+// occlusion decision either follows from a proven bound or is taken in FP32.
+//
+// Bound (per pair s, c; x~ the staged row, x the centred FP32 row):
+//   staging   |x~ - (x_c - x_v)| <= kE |x~| element-wise, kE = 1.0002 (2^-16 + 2^-24)
+//             (2^-24 (1.0001) when every lo is zero);
+//   Gram      |G~_ij - x~_i . x~_j| <= e1 n_i n_j, e1 = 1.01 eps_c, eps_c =
+//             1.01 (n_instr + 1) 2^-22 (the per-MMA-instruction accumulation
+//             model of the general kernel; sampled tile statistics check it);
+//   FP32      |d_fp32 - d| <= gam d, gam = 1.01 (dim + 2) 2^-24;
+//   so |d~ - d_fp32| <= kappa (n_s + n_c)^2, kappa = 1.01 (e1 + 2 kE + kE^2 + gam (1 + kE)^2).
+#include <cuda_bf16.h>
+#include <float.h>
+#include <stddef.h>
+#include <stdint.h>
+#include <stdlib.h>
+
+#include "internal.h"
+#include "tcgen05.cuh"
+
+namespace rnsm {
+
+namespace {
+
+constexpr int kQT = 128;           // threads; warp w reads TMEM lanes 32w..32w+31
+constexpr int kQC = 64;            // raw pool entries per owner
+constexpr int kQCols = 128;        // TMEM columns (N = 128)
+constexpr int kQMaxDim = 128;
+constexpr uint64_t kQWaitNs = 1000000000ull;   // an MMA group takes microseconds
+constexpr int kQErrEvery = 64;     // owners between two tile-error samples
+
+struct PairSmem {
+    alignas(16) float vrow[2][kQMaxDim];   // the owners' FP32 rows
+    const float *rp[2][kQC];               // FP32 row at each position
+    int32_t pid[2][kQC];                   // raw pool ids (-1: empty or the owner)
+    unsigned long long key[2][kQC];        // (distance bits, id) of each raw slot
+    int32_t sid[2][kQC];                   // id at each position (INT32_MAX: none)
+    float sd[2][kQC];                      // exact owner distance at each position
+    float gd[2][kQC];                      // Gram diagonal at each position
+    float nn[2][kQC];                      // bound on the staged row's squared norm
+    float2 pq[2][kQC];                     // column terms of the occlusion test
+    uint32_t occ[2][kQC][2];               // occluders of position c, by position
+    uint32_t live[2][2];                   // live positions (first of their id), per warp
+    uint64_t bar;
+    uint32_t tmem_slot;
+};
+
+__device__ __forceinline__ void owner_sync(int o) {
+    asm volatile("bar.sync %0, 64;" ::"r"(1 + o) : "memory");
+}
+
+__device__ __forceinline__ void max_pos(unsigned int *p, float v) {
+    if (v > 0.f) atomicMax(p, __float_as_uint(v));
+}
+
+// The FP32 prune distance in FP64 (tile statistics only).
+__device__ double dist64(const float *a, const float *b, int dim) {
+    double acc = 0.0;
+    for (int k = 0; k < dim; ++k) {
+        const double d = (double)a[k] - (double)b[k];
+        acc = fma(d, d, acc);
+    }
+    return acc;
+}
+
+// An occlusion test the loose bound left open: the tighter per-pair bound,
+// then the exact FP32 decision.  Returns bit 0 = occluded, bit 1 = decided in FP32.
+__device__ __noinline__ int decide_open(float g, float gs, float ns2, float gc, float nc2, float dvc,
+                                        const float *rs, const float *rc, int dim, float alpha,
+                                        float e1, float kE, float gam) {
+    const float dsc = gs + gc - 2.0f * g;
+    const float sn = sqrtf(ns2) + sqrtf(nc2);
+    const float bc = e1 * sn * sn;                       // Gram accumulation
+    const float E = kE * sn;                             // staging residual of both rows
+    const float bq = E * (2.0f * sqrtf(fmaxf(dsc + bc, 0.f)) + E);
+    const float bf = gam * (fmaxf(dsc, 0.f) + bc + bq);  // the FP32 chain's own rounding
+    const float B = 1.01f * (bc + bq + bf) + 1e-6f * (gs + gc) + 1e-30f;
+    const float slack = 1e-6f * (alpha * (fabsf(dsc) + B) + dvc);
+    if (alpha * (dsc + B) - dvc + slack < 0.f) return 1;
+    if (alpha * (dsc - B) - dvc - slack > 0.f) return 0;
+    const float d = prune_dist(rs, rc, dim, 0);
+    return (fmaf(alpha, d, -dvc) <= 0.f ? 1 : 0) | 2;
+}
+
+__global__ void __launch_bounds__(kQT) prune_pair_kernel(const PruneArgs a, int chunk) {
+    extern __shared__ __align__(1024) unsigned char tile[];
+    __shared__ PairSmem s;
+    __shared__ int64_t sh_i;
+    __shared__ int sh_fail;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int o = warp >> 1, h = warp & 1, t = tid & 63;   // owner of the warp, half, thread in owner
+    const int dim = a.dim, R = a.R;
+    const float alpha = a.alpha;
+    const int U = dim >> 3;                  // 16-byte units of a BF16 row
+    const uint32_t SBO = 16u * (uint32_t)dim;   // bytes between 8-row core-matrix bands
+    const uint32_t region = 128u * 2u * (uint32_t)dim;   // one term (hi or lo) of the tile
+    const float gam = 1.01f * (float)(dim + 2) * 5.9604645e-08f;
+
+    if (tid == 0) {
+        tc::mbar_init(&s.bar, 1);
+        sh_fail = 0;
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(&s.tmem_slot, kQCols);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t taddr = s.tmem_slot;
+    const uint32_t tbase = tc::smem_u32(tile);
+    uint32_t phase = 0;
+    unsigned long long rechecks = 0;
+
+    for (;;) {
+        if (tid == 0) sh_i = atomicAdd(a.work, chunk);
+        __syncthreads();
+        const int64_t i0 = sh_i;
+        if (i0 >= a.n_owners || sh_fail) break;
+        const int64_t i1 = min(a.n_owners, i0 + chunk);
+        // the next owner of the chunk with a pool to prune (uniform over the CTA);
+        // owners whose pools exceed the tile go to the overflow list
+        int64_t cur = i0;
+        auto next_owner = [&]() -> int64_t {
+            while (cur < i1) {
+                const int64_t j = cur++;
+                int64_t cl = 0, ch = 0;
+                if (a.csr_offs) {
+                    cl = a.csr_offs[j];
+                    ch = a.csr_offs[j + 1];
+                }
+                if (a.skip_empty_csr && ch == cl) continue;
+                if ((int64_t)a.lenA + a.lenB + (ch - cl) > kQC) {
+                    if (tid == 0) a.ovf_list[atomicAdd(a.ovf_count, 1ull)] = (int32_t)j;
+                    continue;
+                }
+                return j;
+            }
+            return -1;
+        };
+        for (;;) {
+            const int64_t j0 = next_owner();
+            if (j0 < 0) break;
+            const int64_t j1 = next_owner();
+            const int64_t io = o == 0 ? j0 : j1;   // this warp pair's owner, -1: none
+            // ---- 1. pool, owner row, exact owner distances, order ----------------
+            int32_t owner = -1;
+            int nr = -1;
+            int64_t c_lo = 0;
+            if (io >= 0) {
+                owner = a.owner_ids ? a.owner_ids[io] : (int32_t)(a.owner_base + io);
+                int64_t c_hi = 0;
+                if (a.csr_offs) {
+                    c_lo = a.csr_offs[io];
+                    c_hi = a.csr_offs[io + 1];
+                }
+                nr = (int)((int64_t)a.lenA + a.lenB + (c_hi - c_lo));
+            }
+            const float *orow = owner >= 0 ? seg_row(a.segs, owner, dim) : nullptr;
+            const bool whole = nr >= 0 && a.keep_all_if_fit && nr <= R;   // no tests needed
+            int32_t id = -1;
+            if (t < nr) {
+                if (t < a.lenA) {
+                    id = a.listA[(int64_t)owner * a.lenA + t];
+                } else if (t < a.lenA + a.lenB) {
+                    id = a.listB[io * a.strideB + (t - a.lenA)];
+                    if (id >= 0) id += a.offB;
+                } else {
+                    id = a.csr_ids[c_lo + (t - a.lenA - a.lenB)];
+                }
+                if (id == owner) id = -1;
+            }
+            s.pid[o][t] = id;
+            if (orow)
+                for (int k = t; k < dim; k += 64) s.vrow[o][k] = orow[k];
+            s.occ[o][t][0] = 0u;
+            s.occ[o][t][1] = 0u;
+            const float *xrow = id >= 0 ? seg_row(a.segs, id, dim) : orow;
+            const float dxt = id >= 0 ? prune_dist(orow, xrow, dim, 0) : INFINITY;
+            const int32_t kt = id >= 0 ? id : INT32_MAX;
+            // distances are >= +0 (sums of squares), so their bit patterns order as the
+            // values and (bits << 32 | id) orders as (distance, id)
+            const unsigned long long keyt = ((unsigned long long)__float_as_uint(dxt) << 32) | (uint32_t)kt;
+            s.key[o][t] = keyt;
+            owner_sync(o);
+            {
+                // position: keys below, plus equal keys (repeated ids) at lower slots
+                int r = 0;
+#pragma unroll 8
+                for (int k = 0; k < t; ++k) r += s.key[o][k] <= keyt;
+#pragma unroll 8
+                for (int k = t + 1; k < kQC; ++k) r += s.key[o][k] < keyt;
+                s.sid[o][r] = kt;
+                s.sd[o][r] = dxt;
+                s.rp[o][r] = xrow;
+            }
+            owner_sync(o);
+            // ---- 2. staging in position order; live positions -------------------
+            const int32_t sidt = s.sid[o][t];
+            const bool valid_t = sidt != INT32_MAX;
+            const bool live_t = valid_t && (t == 0 || s.sid[o][t - 1] != sidt);
+            {
+                const unsigned lm = __ballot_sync(0xffffffffu, live_t);
+                if (lane == 0) s.live[o][h] = lm;
+            }
+            const int r = 64 * o + t;   // tile row
+            unsigned char *hrow = tile + (uint32_t)(r >> 3) * SBO + (uint32_t)(r & 7) * 16u;
+            bool lo_any = false;
+            if (!valid_t || whole) {
+                for (int u = 0; u < U; ++u) {
+                    *reinterpret_cast<uint4 *>(hrow + u * 128) = make_uint4(0u, 0u, 0u, 0u);
+                    *reinterpret_cast<uint4 *>(hrow + region + u * 128) = make_uint4(0u, 0u, 0u, 0u);
+                }
+            } else {
+                const float *x = s.rp[o][t];
+                const float *v = s.vrow[o];
+                for (int u0 = 0; u0 < U; u0 += 4) {
+                    float4 xa[4][2];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        if (u0 + k < U) {
+                            xa[k][0] = ldg4(x + 8 * (u0 + k));
+                            xa[k][1] = ldg4(x + 8 * (u0 + k) + 4);
+                        }
+                    }
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const int u = u0 + k;
+                        if (u >= U) break;
+                        const float4 v0 = *reinterpret_cast<const float4 *>(v + 8 * u);
+                        const float4 v1 = *reinterpret_cast<const float4 *>(v + 8 * u + 4);
+                        const f2_t xs[4] = {f2_of(xa[k][0].x, xa[k][0].y), f2_of(xa[k][0].z, xa[k][0].w),
+                                            f2_of(xa[k][1].x, xa[k][1].y), f2_of(xa[k][1].z, xa[k][1].w)};
+                        const f2_t vs[4] = {f2_of(v0.x, v0.y), f2_of(v0.z, v0.w), f2_of(v1.x, v1.y),
+                                            f2_of(v1.z, v1.w)};
+                        uint32_t hw[4], lw[4];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const f2_t y = f2_sub(xs[e], vs[e]);
+                            float y0, y1;
+                            f2_split(y, y0, y1);
+                            const __nv_bfloat162 hb = __floats2bfloat162_rn(y0, y1);
+                            const float2 hf = __bfloat1622float2(hb);
+                            // y - hi is exact in FP32
+                            float t0, t1;
+                            f2_split(f2_sub(y, f2_of(hf.x, hf.y)), t0, t1);
+                            const __nv_bfloat162 lb = __floats2bfloat162_rn(t0, t1);
+                            hw[e] = *reinterpret_cast<const uint32_t *>(&hb);
+                            lw[e] = *reinterpret_cast<const uint32_t *>(&lb);
+                        }
+                        lo_any |= ((lw[0] | lw[1] | lw[2] | lw[3]) & 0x7fff7fffu) != 0u;
+                        *reinterpret_cast<uint4 *>(hrow + u * 128) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                        *reinterpret_cast<uint4 *>(hrow + region + u * 128) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                    }
+                }
+            }
+            tc::fence_async_shared();
+            tc::fence_before_sync();
+            const bool four = __syncthreads_or(lo_any) != 0;
+            tc::fence_after_sync();
+            // ---- 3. the Gram tile -----------------------------------------------
+            const int n_instr = (four ? 4 : 1) * (dim >> 4);
+            const float eps_c = 1.01f * (float)(n_instr + 1) * 2.384185791e-07f;
+            const float e1 = 1.01f * eps_c;
+            const float kE = four ? 1.0002f * (1.52587890625e-05f + 5.9604645e-08f) : 1.0001f * 5.9604645e-08f;
+            const float kappa = 1.01f * (e1 + 2.0f * kE + kE * kE + gam * (1.0f + kE) * (1.0f + kE));
+            const float cb = 2.0f * kappa + 1e-6f;
+            if (tid == 0) {
+                const uint32_t idesc = tc::instr_desc(1u, 128, 128);
+                for (int k = 0; k < (dim >> 4); ++k) {
+                    const uint64_t dh = tc::smem_desc(tbase + k * 256, 128, SBO);
+                    tc::mma_bf16(taddr, dh, dh, idesc, k > 0 ? 1u : 0u);
+                    if (four) {
+                        const uint64_t dl = tc::smem_desc(tbase + region + k * 256, 128, SBO);
+                        tc::mma_bf16(taddr, dl, dh, idesc, 1u);
+                        tc::mma_bf16(taddr, dh, dl, idesc, 1u);
+                        tc::mma_bf16(taddr, dl, dl, idesc, 1u);
+                    }
+                }
+                if (!a.test_withhold_commit) tc::mma_commit(&s.bar);
+            }
+            {
+                // one thread waits; the barrier passes the completion on to the others
+                bool ok = true;
+                if (tid == 0) ok = tc::mbar_wait_bounded(&s.bar, phase, kQWaitNs);
+                if (__syncthreads_or(!ok)) {
+                    if (tid == 0) {
+                        atomicOr(a.err, 64);
+                        sh_fail = 1;
+                        // a second bounded chance for the MMAs before the tensor memory is freed
+                        tc::mbar_wait_bounded(&s.bar, phase, kQWaitNs);
+                    }
+                    break;
+                }
+                phase ^= 1u;
+            }
+            tc::fence_after_sync();
+            // ---- 4. occlusion tests from the tile ---------------------------------
+            const uint32_t tl = taddr + ((uint32_t)(32 * warp) << 16);
+            const int p = 32 * h + lane;             // this lane's position (row s)
+            float gs, ns2;
+            {
+                uint32_t ra[16], rb[16];
+                tc::tmem_ld16(tl + 64 * o + 32 * h, ra);
+                tc::tmem_ld16(tl + 64 * o + 32 * h + 16, rb);
+                tc::tmem_wait_ld();
+                float g = 0.f;
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    g = lane == q ? __uint_as_float(ra[q]) : g;
+                    g = lane == q + 16 ? __uint_as_float(rb[q]) : g;
+                }
+                gs = g;
+                ns2 = fmaxf(g, 0.f) * (1.0f + 2.0f * e1);
+            }
+            const float dvs = s.sd[o][p];
+            const bool valid_s = s.sid[o][p] != INT32_MAX;
+            const float bs = cb * ns2;
+            const float As = alpha * (gs + bs), As2 = alpha * (gs - bs);
+            s.gd[o][p] = gs;
+            s.nn[o][p] = ns2;
+            s.pq[o][p] = valid_s ? make_float2(alpha * (gs + bs) - dvs * (1.0f - 1e-6f),
+                                               alpha * (gs - bs) - dvs * (1.0f + 1e-6f))
+                                 : make_float2(0.f, 0.f);
+            if (a.tile_err && io >= 0 && io % kQErrEvery == 0 && valid_s) {
+                // the tile's owner distance G~_cc against the FP32 and FP64 ones
+                const double d64 = dist64(s.vrow[o], s.rp[o][p], dim);
+                if (d64 != 0.0) {
+                    max_pos(&a.tile_err[0], (float)(fabs((double)gs - d64) / d64));
+                    max_pos(&a.tile_err[1], (float)(fabs((double)dvs - d64) / d64));
+                }
+                max_pos(&a.tile_err[2], fabsf(gs - dvs) / (kappa * ns2 + 1e-30f));
+                atomicAdd(&a.tile_err[3], 1u);
+            }
+            owner_sync(o);
+            if (nr >= 0 && !whole) {
+                const uint64_t lv = (uint64_t)s.live[o][0] | ((uint64_t)s.live[o][1] << 32);
+                // the live positions c after this lane's position s, if s is live
+                const uint64_t am = (lv >> p) & 1ull ? lv & ~((2ull << p) - 1ull) : 0ull;
+                const float m2a = -2.0f * alpha;
+                for (int ch = 0; ch < 4; ++ch) {
+                    const int c0 = 16 * ch;
+                    const uint32_t a16 = (uint32_t)(am >> c0) & 0xffffu;
+                    if (!__any_sync(0xffffffffu, a16 != 0u)) continue;   // occ stays zero
+                    uint32_t rv[16];
+                    tc::tmem_ld16(tl + 64 * o + c0, rv);
+                    tc::tmem_wait_ld();
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) {
+                        const int c = c0 + q;
+                        const float g = __uint_as_float(rv[q]);
+                        const float2 pqc = s.pq[o][c];
+                        const bool act = (a16 >> q) & 1u;
+                        const float up = fmaf(m2a, g, pqc.x + As);
+                        const float dn = fmaf(m2a, g, pqc.y + As2);
+                        bool occl = act && up < 0.f;
+                        if (act && !(up < 0.f) && !(dn > 0.f)) {
+                            const int res = decide_open(g, gs, ns2, s.gd[o][c], s.nn[o][c], s.sd[o][c],
+                                                        s.rp[o][p], s.rp[o][c], dim, alpha, e1, kE, gam);
+                            occl = res & 1;
+                            rechecks += (unsigned long long)(res >> 1);
+                        }
+                        const unsigned m = __ballot_sync(0xffffffffu, occl);
+                        if (lane == 0) s.occ[o][c][h] = m;
+                    }
+                }
+            }
+            tc::fence_before_sync();
+            owner_sync(o);
+            // ---- 5. the greedy walk (one warp per owner) --------------------------
+            if (nr >= 0 && h == 0) {
+                const uint64_t live = (uint64_t)s.live[o][0] | ((uint64_t)s.live[o][1] << 32);
+                const int np = __popcll(live);
+                uint64_t kept = 0;
+                int nk = 0;
+                if (a.keep_all_if_fit && np <= R) {
+                    kept = live;
+                    nk = np;
+                } else {
+                    // a position is decided once every live occluder before it is; it is
+                    // kept iff none of those is kept; the cap keeps the first R kept
+                    const uint64_t oc0 = ((uint64_t)s.occ[o][lane][0] | ((uint64_t)s.occ[o][lane][1] << 32)) & live;
+                    const uint64_t oc1 =
+                        ((uint64_t)s.occ[o][lane + 32][0] | ((uint64_t)s.occ[o][lane + 32][1] << 32)) & live;
+                    const uint64_t b0 = 1ull << lane, b1 = 1ull << (lane + 32);
+                    uint64_t decided = ~live, kall = 0ull;
+                    while (~decided) {
+                        const bool d0 = !(decided & b0), d1 = !(decided & b1);
+                        const bool k0 = d0 && !(oc0 & kall) && !(oc0 & ~decided);
+                        const bool k1 = d1 && !(oc1 & kall) && !(oc1 & ~decided);
+                        const bool r0 = k0 || (d0 && (oc0 & kall));
+                        const bool r1 = k1 || (d1 && (oc1 & kall));
+                        decided |= (uint64_t)__ballot_sync(0xffffffffu, r0) |
+                                   ((uint64_t)__ballot_sync(0xffffffffu, r1) << 32);
+                        kall |= (uint64_t)__ballot_sync(0xffffffffu, k0) |
+                                ((uint64_t)__ballot_sync(0xffffffffu, k1) << 32);
+                    }
+                    while (__popcll(kall) > R) kall &= ~(1ull << (63 - __clzll((long long)kall)));
+                    kept = kall;
+                    nk = __popcll(kall);
+                }
+                int32_t *out = a.out + (a.out_by_index ? io : (int64_t)owner) * R;
+                const bool k0 = (kept >> lane) & 1ull, k1 = (kept >> (lane + 32)) & 1ull;
+                const int p0 = __popcll(kept & ((1ull << lane) - 1ull));
+                const int p1 = __popcll(kept & ((1ull << (lane + 32)) - 1ull));
+                const int32_t id0 = k0 ? s.sid[o][lane] : -1, id1 = k1 ? s.sid[o][lane + 32] : -1;
+                if (k0) out[p0] = id0;
+                if (k1) out[p1] = id1;
+                for (int j = nk + lane; j < R; j += 32) out[j] = -1;
+                if (a.eu) {
+                    const bool e0 = k0 && id0 >= a.emit_lo && id0 < a.emit_hi;
+                    const bool e1b = k1 && id1 >= a.emit_lo && id1 < a.emit_hi;
+                    const unsigned m0 = __ballot_sync(0xffffffffu, e0);
+                    const unsigned m1 = __ballot_sync(0xffffffffu, e1b);
+                    const int cnt = __popc(m0) + __popc(m1);
+                    int base = 0;
+                    if (lane == 0 && cnt) base = (int)atomicAdd(a.ecount, (unsigned long long)cnt);
+                    base = __shfl_sync(0xffffffffu, base, 0);
+                    if (e0) {
+                        const int slot = base + __popc(m0 & lanemask_lt());
+                        a.eu[slot] = id0;
+                        a.ev[slot] = owner;
+                    }
+                    if (e1b) {
+                        const int slot = base + __popc(m0) + __popc(m1 & lanemask_lt());
+                        a.eu[slot] = id1;
+                        a.ev[slot] = owner;
+                    }
+                }
+            }
+            tc::fence_before_sync();
+            __syncthreads();   // the tile, the tensor memory and the owner state are free
+            tc::fence_after_sync();
+        }
+        __syncthreads();   // every thread has read sh_i (and sh_fail) before the next claim
+        if (sh_fail) break;
+    }
+    if (rechecks && a.rechecks) atomicAdd(a.rechecks, rechecks);
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(taddr, kQCols);
+}
+
+}  // namespace
+
+bool prune_pair_ok(int dim, int prec, int metric) {
+    return prec == 1 && metric == 0 && dim >= 16 && dim <= kQMaxDim && dim % 16 == 0;
+}
+
+int prune_pair_max_pool() { return kQC; }
+
+cudaError_t launch_prune_pair(const PruneArgs &in, cudaStream_t st) {
+    if (!prune_pair_ok(in.dim, in.prec, in.metric) || in.R > kQC) return cudaErrorInvalidValue;
+    PruneArgs a = in;
+    // test-only: withhold the MMA completion signal, so every wait runs out
+    a.test_withhold_commit = getenv("RNSM_TEST_WITHHOLD_COMMIT") != nullptr;
+    const size_t dyn = (size_t)512 * a.dim;   // hi and lo terms, 128 rows of 2 dim bytes each
+    auto kern = prune_pair_kernel;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    if (e != cudaSuccess) return e;
+    cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, kern);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, smem_sm = 0, regs_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+    // resident CTAs per SM: shared memory (plus 1 KB reserved per CTA), registers
+    // and the SM's 512 tensor-memory columns
+    int per_sm = smem_sm / (int)(fa.sharedSizeBytes + dyn + 1024);
+    const int by_regs = regs_sm / ((fa.numRegs > 0 ? fa.numRegs : 128) * kQT);
+    if (by_regs < per_sm) per_sm = by_regs;
+    if (per_sm > 512 / kQCols) per_sm = 512 / kQCols;
+    if (per_sm < 1) per_sm = 1;
+    const int chunk = a.skip_empty_csr ? 64 : 8;
+    int64_t grid = (int64_t)sms * per_sm;
+    const int64_t want = (a.n_owners + chunk - 1) / chunk;
+    if (want < grid) grid = want;
+    kern<<<(unsigned)grid, kQT, dyn, st>>>(a, chunk);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace rnsm

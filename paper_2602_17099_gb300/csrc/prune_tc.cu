@@ -31,8 +31,9 @@
 // Staged rows.  One term (kTerms = 1): the library's quantized copies of the
 // rows (BF16, or E4M3 with a per-row scale), re-centred on the owner for L2.
 // Two terms (kTerms = 2, BF16 only): the FP32 rows split into hi = bf16(x)
-// and lo = bf16(x - hi), and the tile accumulates hi*hi + lo*hi + hi*lo;
-// the error left is that of x - hi - lo (about 2^-17 |x|), which removes
+// and lo = bf16(x - hi), and the tile accumulates hi*hi + lo*hi + hi*lo +
+// lo*lo, i.e. the Gram of hi + lo; the error left is that of x - hi - lo
+// (at most 2^-16 |x| element-wise), which removes
 // most re-decisions at large dimensions for twice the staged bytes.
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
@@ -139,7 +140,7 @@ __global__ void __launch_bounds__(kThreads, 2) prune_tc_kernel(const PruneArgs a
     // of (|accumulator| + sum of its |products|), so n instructions err by at most
     // (n + 1) 2^-22 of the sum of all |products|.  The sampled statistics of the
     // tiles (rnsm_stats.tile_error) measure the share of the bound actually used.
-    const int n_instr = (kTerms == 2 ? 3 : 1) * (kFp8 ? dim / 32 : dim / 16);
+    const int n_instr = (kTerms == 2 ? 4 : 1) * (kFp8 ? dim / 32 : dim / 16);
     const float eps_c = 1.01f * (float)(n_instr + 1) * 2.384185791e-07f;
     // the FP32 distance (two chains of dim / 2 terms and their sum): at most
     // (dim + 2) u (sum of |terms|), u = 2^-24 (one rounding per fmaf, the rounded
@@ -201,6 +202,7 @@ __global__ void __launch_bounds__(kThreads, 2) prune_tc_kernel(const PruneArgs a
                         const uint64_t dl = tc::smem_desc(tb + kRegion + k * 256, 128, kSBO);
                         tc::mma_bf16(taddr, dl, dh, idesc, 1u);   // lo * hi
                         tc::mma_bf16(taddr, dh, dl, idesc, 1u);   // hi * lo
+                        tc::mma_bf16(taddr, dl, dl, idesc, 1u);   // lo * lo
                     }
                 }
             }
@@ -897,9 +899,9 @@ int prune_tc_terms(int dim, int prec) {
 
 int prune_tc_max_pool() { return kMaxC; }
 
-cudaError_t launch_prune_tc(const PruneArgs &in, cudaStream_t st) {
-    const int terms = prune_tc_terms(in.dim, in.prec);
-    if (terms == 0) return cudaErrorInvalidValue;
+cudaError_t launch_prune_tc(const PruneArgs &in, cudaStream_t st, int terms) {
+    if (terms == 0) terms = prune_tc_terms(in.dim, in.prec);
+    if (terms == 0 || (terms == 2 && in.prec != 1)) return cudaErrorInvalidValue;
     PruneArgs a = in;
     // test-only: withhold the MMA completion signal, so every wait runs out
     // and the launch ends with the timeout bit of the error word

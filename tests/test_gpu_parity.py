@@ -383,11 +383,16 @@ def test_merge_host_and_device_pivots_agree(rn):
     ("gauss", 512, 128, 64), ("embed", 384, 96, 48), ("gauss", 1024, 70, 32),
     ("sift", 160, 128, 16),
     # pools above 128 overflow to the FP32 general kernel
-    ("embed", 768, 150, 64)])
+    ("embed", 768, 150, 64),
+    # BF16 at L2 and d <= 128 with pools <= 64: two owners per tile (real-valued
+    # rows need the lo term, integer rows do not); R = pool size; d = 16
+    ("deepl2", 96, 64, 32), ("deepl2", 96, 40, 16), ("deepl2", 128, 64, 64),
+    ("gauss", 16, 64, 32), ("gauss", 64, 33, 8), ("sift", 48, 64, 32)])
 def test_low_precision_prune_equals_fp32(rn, prec, kind, d, w, R):
     n = 3000
     X = {"gauss": lambda: gen.gaussian(n, d, 90),
          "deep": lambda: gen.deep_like(n, 91, d=d),
+         "deepl2": lambda: gen.deep_like(n, 94, d=d),
          "sift": lambda: gen.sift_like(n, 92, d=d),
          "embed": lambda: gen.embed_like(n, 93, d=d, n_comp=50)}[kind]()
     metric = oracle.IP if kind in ("deep", "embed") else oracle.L2
@@ -407,7 +412,9 @@ def test_low_precision_merge_equals_fp32(rn, prec):
                          ([gen.sift_like(4000, 95, d=128), gen.sift_like(3000, 96, d=128)],
                           oracle.L2),
                          ([gen.deep_like(3000, 97, d=96), gen.deep_like(2500, 98, d=96)],
-                          oracle.IP)):
+                          oracle.IP),
+                         ([gen.deep_like(6000, 99, d=96), gen.deep_like(5000, 100, d=96)],
+                          oracle.L2)):
         R, L = (16, 32) if segs[0].shape[1] == 32 else (32, 64)
         gs = [oracle.build_graph(s, R, L, 1.2, metric=metric) for s in segs]
         tsegs = [(dev(s), dev(g), e) for s, (g, e) in zip(segs, gs)]

@@ -22,18 +22,23 @@ def rn():
     return rnsm
 
 
-def test_tile_wait_runs_out_and_the_context_stays_usable(rn, monkeypatch):
+# L2 at d = 64 with pools of 40: the two-owner pair tile; inner product: the
+# general tile (one owner per CTA)
+@pytest.mark.parametrize("metric", [0, 1])
+def test_tile_wait_runs_out_and_the_context_stays_usable(rn, monkeypatch, metric):
     n = 2000
     X = torch.from_numpy(gen.gaussian(n, 64, 5)).cuda()
+    if metric == 1:
+        X = X / X.norm(dim=1, keepdim=True)
     rng = np.random.default_rng(3)
     owners = torch.from_numpy(rng.choice(n, 300, replace=False).astype(np.int32)).cuda()
     pool = torch.from_numpy(rng.integers(-1, n, size=(300, 40)).astype(np.int32)).cuda()
-    want = rn.prune(X, owners, pool, 16, 1.2)
+    want = rn.prune(X, owners, pool, 16, 1.2, metric=metric)
     monkeypatch.setenv("RNSM_TEST_WITHHOLD_COMMIT", "1")
     with pytest.raises(rn.RnsmError) as ei:
-        rn.prune(X, owners, pool, 16, 1.2, prec=rn.BF16)
+        rn.prune(X, owners, pool, 16, 1.2, metric=metric, prec=rn.BF16)
     assert ei.value.status == rn.ETIMEOUT
     monkeypatch.delenv("RNSM_TEST_WITHHOLD_COMMIT")
     torch.cuda.synchronize()          # no sticky error: the context still works
-    got = rn.prune(X, owners, pool, 16, 1.2, prec=rn.BF16)
+    got = rn.prune(X, owners, pool, 16, 1.2, metric=metric, prec=rn.BF16)
     assert torch.equal(got, want)
