@@ -65,16 +65,15 @@ constexpr int kQErrEvery = 64;     // owners between two tile-error samples
 
 struct PairSmem {
     alignas(16) float vrow[2][kQMaxDim];   // the owners' FP32 rows
-    const float *rp[2][kQC];               // FP32 row at each position
-    int32_t pid[2][kQC];                   // raw pool ids (-1: empty or the owner)
-    unsigned long long key[2][kQC];        // (distance bits, id) of each raw slot
-    int32_t sid[2][kQC];                   // id at each position (INT32_MAX: none)
-    float sd[2][kQC];                      // exact owner distance at each position
-    float gd[2][kQC];                      // Gram diagonal at each position
+    unsigned long long key[2][kQC];        // (distance bits, id) of each slot; ~0: none
+    unsigned long long ltm[2][kQC];        // slots before each slot in (distance, id) order
+    const float *rp[2][kQC];               // FP32 row of each slot
+    float sd[2][kQC];                      // exact owner distance of each slot
+    float gd[2][kQC];                      // Gram diagonal
     float nn[2][kQC];                      // bound on the staged row's squared norm
     float2 pq[2][kQC];                     // column terms of the occlusion test
-    uint32_t occ[2][kQC][2];               // occluders of position c, by position
-    uint32_t live[2][2];                   // live positions (first of their id), per warp
+    uint32_t occ[2][kQC][2];               // occluders of slot c, by slot
+    uint32_t live[2][2];                   // valid slots (ids not repeated), per warp
     uint64_t bar;
     uint32_t tmem_slot;
 };
@@ -177,7 +176,7 @@ __global__ void __launch_bounds__(kQT) prune_pair_kernel(const PruneArgs a, int 
             if (j0 < 0) break;
             const int64_t j1 = next_owner();
             const int64_t io = o == 0 ? j0 : j1;   // this warp pair's owner, -1: none
-            // ---- 1. pool, owner row, exact owner distances, order ----------------
+            // ---- 1. pool and owner row ------------------------------------------
             int32_t owner = -1;
             int nr = -1;
             int64_t c_lo = 0;
@@ -204,57 +203,47 @@ __global__ void __launch_bounds__(kQT) prune_pair_kernel(const PruneArgs a, int 
                 }
                 if (id == owner) id = -1;
             }
-            s.pid[o][t] = id;
             if (orow)
                 for (int k = t; k < dim; k += 64) s.vrow[o][k] = orow[k];
             s.occ[o][t][0] = 0u;
             s.occ[o][t][1] = 0u;
-            const float *xrow = id >= 0 ? seg_row(a.segs, id, dim) : orow;
-            const float dxt = id >= 0 ? prune_dist(orow, xrow, dim, 0) : INFINITY;
-            const int32_t kt = id >= 0 ? id : INT32_MAX;
-            // distances are >= +0 (sums of squares), so their bit patterns order as the
-            // values and (bits << 32 | id) orders as (distance, id)
-            const unsigned long long keyt = ((unsigned long long)__float_as_uint(dxt) << 32) | (uint32_t)kt;
-            s.key[o][t] = keyt;
-            owner_sync(o);
+            // a repeated id keeps its first slot (same row, same distance: the FP32
+            // prune keeps the first of equal (distance, id) entries)
             {
-                // position: keys below, plus equal keys (repeated ids) at lower slots
-                int r = 0;
-#pragma unroll 8
-                for (int k = 0; k < t; ++k) r += s.key[o][k] <= keyt;
-#pragma unroll 8
-                for (int k = t + 1; k < kQC; ++k) r += s.key[o][k] < keyt;
-                s.sid[o][r] = kt;
-                s.sd[o][r] = dxt;
-                s.rp[o][r] = xrow;
+                const unsigned same = __match_any_sync(0xffffffffu, id);
+                if (same & lanemask_lt()) id = -1;
+                if (h == 0) s.key[o][t] = (unsigned long long)(uint32_t)id;   // ids only, for now
             }
             owner_sync(o);
-            // ---- 2. staging in position order; live positions -------------------
-            const int32_t sidt = s.sid[o][t];
-            const bool valid_t = sidt != INT32_MAX;
-            const bool live_t = valid_t && (t == 0 || s.sid[o][t - 1] != sidt);
-            {
-                const unsigned lm = __ballot_sync(0xffffffffu, live_t);
-                if (lane == 0) s.live[o][h] = lm;
+            if (h == 1 && id >= 0) {
+                for (int k = 0; k < 32; ++k)
+                    if ((int32_t)(uint32_t)s.key[o][k] == id) id = -1;
             }
-            const int r = 64 * o + t;   // tile row
+            const bool valid_t = id >= 0;
+            // ---- 2. one pass over the row: exact owner distance and the tile terms
+            const float *xrow = valid_t ? seg_row(a.segs, id, dim) : orow;
+            const int r = 64 * o + t;   // tile row: this slot
             unsigned char *hrow = tile + (uint32_t)(r >> 3) * SBO + (uint32_t)(r & 7) * 16u;
             bool lo_any = false;
-            if (!valid_t || whole) {
+            float dxt = INFINITY;
+            if (!valid_t) {
                 for (int u = 0; u < U; ++u) {
                     *reinterpret_cast<uint4 *>(hrow + u * 128) = make_uint4(0u, 0u, 0u, 0u);
                     *reinterpret_cast<uint4 *>(hrow + region + u * 128) = make_uint4(0u, 0u, 0u, 0u);
                 }
             } else {
-                const float *x = s.rp[o][t];
+                // the FP32 prune distance, chains E (even dimensions) and O (odd) over
+                // v - x in increasing order, exactly as prune_dist; the same v - x,
+                // split into hi + lo, is the staged row (centred on the owner)
+                f2_t acc = 0ull;
                 const float *v = s.vrow[o];
                 for (int u0 = 0; u0 < U; u0 += 4) {
                     float4 xa[4][2];
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
                         if (u0 + k < U) {
-                            xa[k][0] = ldg4(x + 8 * (u0 + k));
-                            xa[k][1] = ldg4(x + 8 * (u0 + k) + 4);
+                            xa[k][0] = ldg4(xrow + 8 * (u0 + k));
+                            xa[k][1] = ldg4(xrow + 8 * (u0 + k) + 4);
                         }
                     }
 #pragma unroll
@@ -270,7 +259,8 @@ __global__ void __launch_bounds__(kQT) prune_pair_kernel(const PruneArgs a, int 
                         uint32_t hw[4], lw[4];
 #pragma unroll
                         for (int e = 0; e < 4; ++e) {
-                            const f2_t y = f2_sub(xs[e], vs[e]);
+                            const f2_t y = f2_sub(vs[e], xs[e]);
+                            acc = f2_fma(y, y, acc);
                             float y0, y1;
                             f2_split(y, y0, y1);
                             const __nv_bfloat162 hb = __floats2bfloat162_rn(y0, y1);
@@ -282,16 +272,33 @@ __global__ void __launch_bounds__(kQT) prune_pair_kernel(const PruneArgs a, int 
                             hw[e] = *reinterpret_cast<const uint32_t *>(&hb);
                             lw[e] = *reinterpret_cast<const uint32_t *>(&lb);
                         }
+                        if (whole) {   // no tests: the tile rows stay zero
+                            hw[0] = hw[1] = hw[2] = hw[3] = 0u;
+                            lw[0] = lw[1] = lw[2] = lw[3] = 0u;
+                        }
                         lo_any |= ((lw[0] | lw[1] | lw[2] | lw[3]) & 0x7fff7fffu) != 0u;
                         *reinterpret_cast<uint4 *>(hrow + u * 128) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
                         *reinterpret_cast<uint4 *>(hrow + region + u * 128) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
                     }
                 }
+                dxt = chain2_final(acc, 0);
+            }
+            // distances are >= +0 (sums of squares), so their bit patterns order as the
+            // values and (bits << 32 | id) orders as (distance, id); after the repeats are
+            // dropped the valid keys are distinct
+            const unsigned long long keyt =
+                valid_t ? ((unsigned long long)__float_as_uint(dxt) << 32) | (uint32_t)id : ~0ull;
+            {
+                const unsigned lm = __ballot_sync(0xffffffffu, valid_t);
+                if (lane == 0) s.live[o][h] = lm;
             }
             tc::fence_async_shared();
             tc::fence_before_sync();
-            const bool four = __syncthreads_or(lo_any) != 0;
+            const bool four = __syncthreads_or(lo_any) != 0;   // ids read above are no longer needed
             tc::fence_after_sync();
+            s.key[o][t] = keyt;
+            s.sd[o][t] = dxt;
+            s.rp[o][t] = xrow;
             // ---- 3. the Gram tile -----------------------------------------------
             const int n_instr = (four ? 4 : 1) * (dim >> 4);
             const float eps_c = 1.01f * (float)(n_instr + 1) * 2.384185791e-07f;
@@ -313,6 +320,14 @@ __global__ void __launch_bounds__(kQT) prune_pair_kernel(const PruneArgs a, int 
                 }
                 if (!a.test_withhold_commit) tc::mma_commit(&s.bar);
             }
+            // while the MMAs run: the slots before this one in (distance, id) order
+            owner_sync(o);
+            uint64_t ltm = 0ull;
+            if (valid_t) {
+#pragma unroll
+                for (int k = 0; k < kQC; ++k) ltm |= s.key[o][k] < keyt ? 1ull << k : 0ull;
+            }
+            s.ltm[o][t] = ltm;
             {
                 // one thread waits; the barrier passes the completion on to the others
                 bool ok = true;
@@ -331,7 +346,7 @@ __global__ void __launch_bounds__(kQT) prune_pair_kernel(const PruneArgs a, int 
             tc::fence_after_sync();
             // ---- 4. occlusion tests from the tile ---------------------------------
             const uint32_t tl = taddr + ((uint32_t)(32 * warp) << 16);
-            const int p = 32 * h + lane;             // this lane's position (row s)
+            const int p = t;                         // this lane's slot (row s)
             float gs, ns2;
             {
                 uint32_t ra[16], rb[16];
@@ -347,18 +362,17 @@ __global__ void __launch_bounds__(kQT) prune_pair_kernel(const PruneArgs a, int 
                 gs = g;
                 ns2 = fmaxf(g, 0.f) * (1.0f + 2.0f * e1);
             }
-            const float dvs = s.sd[o][p];
-            const bool valid_s = s.sid[o][p] != INT32_MAX;
+            const float dvs = dxt;
             const float bs = cb * ns2;
             const float As = alpha * (gs + bs), As2 = alpha * (gs - bs);
             s.gd[o][p] = gs;
             s.nn[o][p] = ns2;
-            s.pq[o][p] = valid_s ? make_float2(alpha * (gs + bs) - dvs * (1.0f - 1e-6f),
+            s.pq[o][p] = valid_t ? make_float2(alpha * (gs + bs) - dvs * (1.0f - 1e-6f),
                                                alpha * (gs - bs) - dvs * (1.0f + 1e-6f))
                                  : make_float2(0.f, 0.f);
-            if (a.tile_err && io >= 0 && io % kQErrEvery == 0 && valid_s) {
+            if (a.tile_err && io >= 0 && io % kQErrEvery == 0 && valid_t && !whole) {
                 // the tile's owner distance G~_cc against the FP32 and FP64 ones
-                const double d64 = dist64(s.vrow[o], s.rp[o][p], dim);
+                const double d64 = dist64(s.vrow[o], xrow, dim);
                 if (d64 != 0.0) {
                     max_pos(&a.tile_err[0], (float)(fabs((double)gs - d64) / d64));
                     max_pos(&a.tile_err[1], (float)(fabs((double)dvs - d64) / d64));
@@ -367,10 +381,10 @@ __global__ void __launch_bounds__(kQT) prune_pair_kernel(const PruneArgs a, int 
                 atomicAdd(&a.tile_err[3], 1u);
             }
             owner_sync(o);
+            const uint64_t live = (uint64_t)s.live[o][0] | ((uint64_t)s.live[o][1] << 32);
             if (nr >= 0 && !whole) {
-                const uint64_t lv = (uint64_t)s.live[o][0] | ((uint64_t)s.live[o][1] << 32);
-                // the live positions c after this lane's position s, if s is live
-                const uint64_t am = (lv >> p) & 1ull ? lv & ~((2ull << p) - 1ull) : 0ull;
+                // the live slots c after this lane's slot s in the order, if s is live
+                const uint64_t am = valid_t ? live & ~ltm & ~(1ull << p) : 0ull;
                 const float m2a = -2.0f * alpha;
                 for (int ch = 0; ch < 4; ++ch) {
                     const int c0 = 16 * ch;
@@ -390,7 +404,7 @@ __global__ void __launch_bounds__(kQT) prune_pair_kernel(const PruneArgs a, int 
                         bool occl = act && up < 0.f;
                         if (act && !(up < 0.f) && !(dn > 0.f)) {
                             const int res = decide_open(g, gs, ns2, s.gd[o][c], s.nn[o][c], s.sd[o][c],
-                                                        s.rp[o][p], s.rp[o][c], dim, alpha, e1, kE, gam);
+                                                        xrow, s.rp[o][c], dim, alpha, e1, kE, gam);
                             occl = res & 1;
                             rechecks += (unsigned long long)(res >> 1);
                         }
@@ -402,20 +416,62 @@ __global__ void __launch_bounds__(kQT) prune_pair_kernel(const PruneArgs a, int 
             tc::fence_before_sync();
             owner_sync(o);
             // ---- 5. the greedy walk (one warp per owner) --------------------------
+            if (h == 1) {
+                // meanwhile the other warp brings the rows of this warp pair's next owner
+                // (same chunk) into L2
+                int64_t pc = cur, nx = -1;
+                for (int k = 0; k <= o; ++k) {
+                    nx = -1;
+                    while (pc < i1) {
+                        const int64_t j = pc++;
+                        int64_t cl = 0, ch = 0;
+                        if (a.csr_offs) {
+                            cl = a.csr_offs[j];
+                            ch = a.csr_offs[j + 1];
+                        }
+                        if ((a.skip_empty_csr && ch == cl) || (int64_t)a.lenA + a.lenB + (ch - cl) > kQC)
+                            continue;
+                        nx = j;
+                        break;
+                    }
+                }
+                if (nx >= 0) {
+                    const int32_t on = a.owner_ids ? a.owner_ids[nx] : (int32_t)(a.owner_base + nx);
+                    const int64_t cl = a.csr_offs ? a.csr_offs[nx] : 0;
+                    const int nrn = (int)((int64_t)a.lenA + a.lenB + ((a.csr_offs ? a.csr_offs[nx + 1] : 0) - cl));
+                    for (int j = lane; j <= nrn; j += 32) {
+                        int32_t idn = on;   // j == nrn: the owner
+                        if (j < nrn) {
+                            if (j < a.lenA) {
+                                idn = a.listA[(int64_t)on * a.lenA + j];
+                            } else if (j < a.lenA + a.lenB) {
+                                idn = a.listB[nx * a.strideB + (j - a.lenA)];
+                                if (idn >= 0) idn += a.offB;
+                            } else {
+                                idn = a.csr_ids[cl + (j - a.lenA - a.lenB)];
+                            }
+                        }
+                        if (idn < 0) continue;
+                        const char *row = reinterpret_cast<const char *>(seg_row(a.segs, idn, dim));
+                        for (int l = 0; l < dim * 4; l += 128) prefetch_l2(row + l);
+                    }
+                }
+            }
             if (nr >= 0 && h == 0) {
-                const uint64_t live = (uint64_t)s.live[o][0] | ((uint64_t)s.live[o][1] << 32);
+                // slots l and l + 32 of lane l; occluders of slot c: live slots before c
+                // in the order that occlude it
                 const int np = __popcll(live);
+                const uint64_t lt0 = s.ltm[o][lane], lt1 = s.ltm[o][lane + 32];
                 uint64_t kept = 0;
-                int nk = 0;
                 if (a.keep_all_if_fit && np <= R) {
                     kept = live;
-                    nk = np;
                 } else {
-                    // a position is decided once every live occluder before it is; it is
-                    // kept iff none of those is kept; the cap keeps the first R kept
-                    const uint64_t oc0 = ((uint64_t)s.occ[o][lane][0] | ((uint64_t)s.occ[o][lane][1] << 32)) & live;
+                    // a slot is decided once every live occluder before it is; it is kept
+                    // iff none of those is kept
+                    const uint64_t oc0 =
+                        ((uint64_t)s.occ[o][lane][0] | ((uint64_t)s.occ[o][lane][1] << 32)) & lt0 & live;
                     const uint64_t oc1 =
-                        ((uint64_t)s.occ[o][lane + 32][0] | ((uint64_t)s.occ[o][lane + 32][1] << 32)) & live;
+                        ((uint64_t)s.occ[o][lane + 32][0] | ((uint64_t)s.occ[o][lane + 32][1] << 32)) & lt1 & live;
                     const uint64_t b0 = 1ull << lane, b1 = 1ull << (lane + 32);
                     uint64_t decided = ~live, kall = 0ull;
                     while (~decided) {
@@ -429,15 +485,17 @@ __global__ void __launch_bounds__(kQT) prune_pair_kernel(const PruneArgs a, int 
                         kall |= (uint64_t)__ballot_sync(0xffffffffu, k0) |
                                 ((uint64_t)__ballot_sync(0xffffffffu, k1) << 32);
                     }
-                    while (__popcll(kall) > R) kall &= ~(1ull << (63 - __clzll((long long)kall)));
                     kept = kall;
-                    nk = __popcll(kall);
                 }
+                // output in (distance, id) order: a kept slot's index is the number of kept
+                // slots before it; the cap keeps the first R
+                const int nk = min(__popcll(kept), R);
                 int32_t *out = a.out + (a.out_by_index ? io : (int64_t)owner) * R;
-                const bool k0 = (kept >> lane) & 1ull, k1 = (kept >> (lane + 32)) & 1ull;
-                const int p0 = __popcll(kept & ((1ull << lane) - 1ull));
-                const int p1 = __popcll(kept & ((1ull << (lane + 32)) - 1ull));
-                const int32_t id0 = k0 ? s.sid[o][lane] : -1, id1 = k1 ? s.sid[o][lane + 32] : -1;
+                const int p0 = __popcll(kept & lt0), p1 = __popcll(kept & lt1);
+                const bool k0 = ((kept >> lane) & 1ull) && p0 < R;
+                const bool k1 = ((kept >> (lane + 32)) & 1ull) && p1 < R;
+                const int32_t id0 = k0 ? (int32_t)(uint32_t)s.key[o][lane] : -1;
+                const int32_t id1 = k1 ? (int32_t)(uint32_t)s.key[o][lane + 32] : -1;
                 if (k0) out[p0] = id0;
                 if (k1) out[p1] = id1;
                 for (int j = nk + lane; j < R; j += 32) out[j] = -1;
