@@ -1127,6 +1127,10 @@ rnsm_status rnsm_merge(const rnsm_segment *segs, int32_t m, const rnsm_params *p
                 np[(size_t)s] = np_;
                 nf[(size_t)s] = nf_;
             }
+            // followers of one pivot start from the same seeds: searched side by side
+            // they share rows in L2 (the order of independent queries changes no result)
+            CK(group_followers(pivot_of, followers, nf[(size_t)s], ns, mb.rk_keys, mb.rk_vals,
+                               mb.rk_offs, mb.rk_cursor, mb.rk_scan, mb.rk_scan_bytes, st));
             tm.end(t3);
         }
     }

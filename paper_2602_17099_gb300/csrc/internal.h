@@ -149,6 +149,13 @@ cudaError_t launch_prune_pair(const PruneArgs &a, cudaStream_t st);
 cudaError_t launch_quantize(const SegTable &segs, int64_t n, int32_t dim, int prec, void *q,
                             void *q_lo, float *scale, float *err, float *norm, cudaStream_t st);
 
+// Reorders the follower list so that the followers of one pivot are adjacent
+// (keys, vals: nf scratch entries each; offs, cursor, scan: counting-sort scratch
+// for n keys).  Order inside a pivot's group is unspecified.
+cudaError_t group_followers(const int32_t *pivot_of, int32_t *followers, int64_t nf, int64_t n,
+                            int32_t *keys, int32_t *vals, int64_t *offs, int32_t *cursor,
+                            void *scan_tmp, size_t scan_tmp_bytes, cudaStream_t st);
+
 // Counting sort of (key, val) pairs by key into CSR (K3).
 // keys/vals [cap], the number of valid pairs at *count (device) or n_host.
 cudaError_t launch_bucket(const int32_t *keys, const int32_t *vals, int64_t cap,
