@@ -794,6 +794,7 @@ struct MergeBufs {
     void *rk_scan;
     size_t rk_scan_bytes;
     int32_t *pivot_of, *pivots, *followers;   // [N] each, segment s at off[s]
+    int32_t *ord, *rank;                      // locality order of each source and positions
     void *piv_tmp;
     int32_t *res;                          // [res_rows * L]
     int32_t *eu, *ev;
@@ -817,6 +818,8 @@ void carve_merge(Bump &b, const rnsm_params &p, int64_t nmax, int64_t n_all, int
     m.pivot_of = b.take<int32_t>(n_all);
     m.pivots = b.take<int32_t>(n_all);
     m.followers = b.take<int32_t>(n_all);
+    m.ord = b.take<int32_t>(n_all);
+    m.rank = b.take<int32_t>(n_all);
     m.piv_tmp = b.take<char>(pivot_tmp_bytes(nmax));
     m.res = b.take<int32_t>(res_rows * p.L);
     m.eu = b.take<int32_t>(nmax * p.R);
@@ -1054,12 +1057,16 @@ rnsm_status rnsm_merge(const rnsm_segment *segs, int32_t m, const rnsm_params *p
             np[(size_t)s] = segs[s].n;
         }
     } else if (!srcs.empty()) {
-        // S1: neighbour expansion of every source in its own graph, one launch
+        // S1: neighbour expansion of every source in its own graph, one launch,
+        // queries in locality order
         const int t1 = tm.begin(1);
         std::vector<SearchJob> jobs;
         int64_t total = 0;
         for (int32_t s : srcs) {
-            jobs.push_back(make_job(segs[s], segs[s].vecs, nullptr,
+            CK(launch_locality_order(segs[s].vecs, segs[s].n, dim, mb.rk_keys, mb.rk_vals,
+                                     mb.rk_offs, mb.rk_cursor, mb.rk_scan, mb.rk_scan_bytes,
+                                     mb.ord + tab.off[s], mb.rank + tab.off[s], st));
+            jobs.push_back(make_job(segs[s], segs[s].vecs, mb.ord + tab.off[s],
                                     mb.nplus + tab.off[s] * p.k_plus, total));
             total += segs[s].n;
         }
@@ -1127,10 +1134,11 @@ rnsm_status rnsm_merge(const rnsm_segment *segs, int32_t m, const rnsm_params *p
                 np[(size_t)s] = np_;
                 nf[(size_t)s] = nf_;
             }
-            // followers of one pivot start from the same seeds: searched side by side
-            // they share rows in L2 (the order of independent queries changes no result)
-            CK(group_followers(pivot_of, followers, nf[(size_t)s], ns, mb.rk_keys, mb.rk_vals,
-                               mb.rk_offs, mb.rk_cursor, mb.rk_scan, mb.rk_scan_bytes, st));
+            // schedule of S4 and S5: pivots in locality order, each pivot's followers
+            // (which start from the same seeds) side by side
+            CK(order_search_lists(mb.rank + tab.off[s], pivot_of, pivots, np[(size_t)s], followers,
+                                  nf[(size_t)s], ns, mb.rk_keys, mb.rk_vals, mb.rk_offs,
+                                  mb.rk_cursor, mb.rk_scan, mb.rk_scan_bytes, st));
             tm.end(t3);
         }
     }
@@ -1254,8 +1262,8 @@ rnsm_status rnsm_merge(const rnsm_segment *segs, int32_t m, const rnsm_params *p
         std::vector<SearchJob> j5 = jobs_of(groups[gi].first, groups[gi].second, true, tot5);
         // capture only what replays unchanged: one group, no autotuning inside
         const bool want_graph = (p.flags & RNSM_FLAG_GRAPH) && groups.size() == 1 &&
-                                !search_would_tune(dim, p.L, tot4) &&
-                                !search_would_tune(dim, p.ef_slide, tot5);
+                                !search_would_tune(dim, p.L, kSeedConst, tot4) &&
+                                !search_would_tune(dim, p.ef_slide, kSeedTable, tot5);
         TRY(upload_jobs(j4, tot4, mb.jobs4, st));
         TRY(upload_jobs(j5, tot5, mb.jobs5, st));
         for (size_t e = groups[gi].first; e < groups[gi].second; ++e) {

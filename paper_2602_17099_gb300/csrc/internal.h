@@ -75,10 +75,8 @@ struct SearchArgs {
 
 cudaError_t launch_search(const SearchArgs &a, cudaStream_t st);
 cudaError_t launch_search_jobs(const SearchArgs &a, int var, cudaStream_t st);
-// Launch-shape variant the search autotuner chose for (dim, ef), -1 if none yet.
-int search_variant_for(int dim, int ef);
-// True if a launch of nq queries would run the autotuner (timed slices, host waits).
-bool search_would_tune(int dim, int ef, int64_t nq);
+// True if a launch of nq queries would run the autotuner (timed chunks, host waits).
+bool search_would_tune(int dim, int ef, int seed_mode, int64_t nq);
 
 // Occlusion prune (UpdateGraph) of a batch of owners over a segment table.
 // Owner i is global id owner_ids ? owner_ids[i] : owner_base + i.  Its pool
@@ -149,12 +147,20 @@ cudaError_t launch_prune_pair(const PruneArgs &a, cudaStream_t st);
 cudaError_t launch_quantize(const SegTable &segs, int64_t n, int32_t dim, int prec, void *q,
                             void *q_lo, float *scale, float *err, float *norm, cudaStream_t st);
 
-// Reorders the follower list so that the followers of one pivot are adjacent
-// (keys, vals: nf scratch entries each; offs, cursor, scan: counting-sort scratch
-// for n keys).  Order inside a pivot's group is unspecified.
-cudaError_t group_followers(const int32_t *pivot_of, int32_t *followers, int64_t nf, int64_t n,
-                            int32_t *keys, int32_t *vals, int64_t *offs, int32_t *cursor,
-                            void *scan_tmp, size_t scan_tmp_bytes, cudaStream_t st);
+// Query schedule (schedule.cu).  launch_locality_order: the n rows of x
+// counting-sorted by a random-hyperplane locality key (order) and each row's
+// position in that order (rank); keys, vals: n scratch entries each; offs,
+// cursor, scan: counting-sort scratch for min(n, 4096) keys.
+cudaError_t launch_locality_order(const float *x, int64_t n, int32_t dim, int32_t *keys,
+                                  int32_t *vals, int64_t *offs, int32_t *cursor, void *scan_tmp,
+                                  size_t scan_tmp_bytes, int32_t *order, int32_t *rank,
+                                  cudaStream_t st);
+// Pivots sorted by rank, followers by the rank of their pivot (counting-sort
+// scratch for n keys); the order inside one pivot's followers is unspecified.
+cudaError_t order_search_lists(const int32_t *rank, const int32_t *pivot_of, int32_t *pivots,
+                               int64_t np, int32_t *followers, int64_t nf, int64_t n,
+                               int32_t *keys, int32_t *vals, int64_t *offs, int32_t *cursor,
+                               void *scan_tmp, size_t scan_tmp_bytes, cudaStream_t st);
 
 // Counting sort of (key, val) pairs by key into CSR (K3).
 // keys/vals [cap], the number of valid pairs at *count (device) or n_host.

@@ -111,27 +111,7 @@ int grid_n(int64_t n) {
     return g < 1 ? 1 : (int)g;
 }
 
-__global__ void fol_keys_kernel(int64_t nf, const int32_t *pivot_of, const int32_t *followers,
-                                int32_t *keys, int32_t *vals) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nf;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t f = followers[i];
-        keys[i] = pivot_of[f];
-        vals[i] = f;
-    }
-}
-
 }  // namespace
-
-cudaError_t group_followers(const int32_t *pivot_of, int32_t *followers, int64_t nf, int64_t n,
-                            int32_t *keys, int32_t *vals, int64_t *offs, int32_t *cursor,
-                            void *scan_tmp, size_t scan_tmp_bytes, cudaStream_t st) {
-    if (nf <= 0) return cudaSuccess;
-    fol_keys_kernel<<<grid_n(nf), 256, 0, st>>>(nf, pivot_of, followers, keys, vals);
-    note_launches(1);
-    return launch_bucket(keys, vals, nf, nullptr, n, 0, offs, cursor, followers, scan_tmp,
-                         scan_tmp_bytes, st);
-}
 
 size_t pivot_tmp_bytes(int64_t n) {
     return (size_t)n * (sizeof(unsigned long long) + 2) + 256;

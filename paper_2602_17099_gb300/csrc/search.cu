@@ -40,91 +40,100 @@ SearchArgs subrange(const SearchArgs &a, int64_t q0, int64_t q1) {
     return b;
 }
 
-// Autotuner: the first launch with at least kTuneMin queries for a (dim,
-// beam) shape runs every variant on the same slices of its queries: one
-// untimed warm-up slice, then kTuneReps timed slices, each run by every
-// variant in turn (order alternating between slices; CUDA events on the
-// launching stream).  The variant with the smallest total time is kept for
-// later launches.  Every variant computes the same results, so running a
-// slice again only costs time, and the comparison is on identical work.
-constexpr int64_t kTuneWarm = 2000;
-constexpr int64_t kTuneSlice = 8000;
-constexpr int kTuneReps = 3;
-constexpr int64_t kTuneMin = kTuneWarm + kTuneReps * kTuneSlice + 10000;
+// Autotuner: the first launch of a (dim, beam, seed mode) shape with at least
+// kTuneChunks * kTuneMinChunk queries runs as kTuneChunks consecutive chunks
+// spread over its whole query list, the variants taking turns (the order
+// rotating every round), each chunk timed with CUDA events on the launching
+// stream and its distance computations counted.  The variant with the least
+// time per distance computation is kept for later launches of that shape.
+// Every query runs once, with final results (all variants compute the same
+// beams); normalising by the distance count makes chunks of different
+// difficulty comparable, and spreading the chunks over the list keeps the
+// comparison representative when the queries come in locality order.
+constexpr int kTuneChunks = 4 * kVariants;
+constexpr int64_t kTuneMinChunk = 4000;
+struct TuneKey {
+    int dim, efmax, seed_mode;
+    bool operator<(const TuneKey &o) const {
+        return dim != o.dim ? dim < o.dim : efmax != o.efmax ? efmax < o.efmax : seed_mode < o.seed_mode;
+    }
+};
 std::mutex g_tune_mu;
-std::map<std::pair<int, int>, int> g_tuned;
+std::map<TuneKey, int> g_tuned;
 
 int efmax_of(int ef) { return ef <= 32 ? 32 : ef <= 64 ? 64 : ef <= 128 ? 128 : 256; }
 
-}  // namespace
-
-int search_variant_for(int dim, int ef) {
-    std::lock_guard<std::mutex> lk(g_tune_mu);
-    auto it = g_tuned.find({dim, efmax_of(ef)});
-    return it == g_tuned.end() ? -1 : it->second;
+int forced_variant() {
+    const char *force = getenv("RNSM_SEARCH_VARIANT");
+    return force && force[0] >= '0' && force[0] < '0' + kVariants ? force[0] - '0' : -1;
 }
 
-bool search_would_tune(int dim, int ef, int64_t nq) {
-    const char *force = getenv("RNSM_SEARCH_VARIANT");
-    if (force && force[0] >= '0' && force[0] < '0' + kVariants) return false;
-    if (nq < kTuneMin) return false;
-    return search_variant_for(dim, ef) < 0;
+}  // namespace
+
+bool search_would_tune(int dim, int ef, int seed_mode, int64_t nq) {
+    if (forced_variant() >= 0 || nq < kTuneChunks * kTuneMinChunk) return false;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    return g_tuned.find({dim, efmax_of(ef), seed_mode}) == g_tuned.end();
 }
 
 cudaError_t launch_search(const SearchArgs &a, cudaStream_t st) {
     if (a.nq <= 0) return cudaSuccess;
     if (!search_dim_supported(a.dim)) return cudaErrorInvalidValue;
-    const char *force = getenv("RNSM_SEARCH_VARIANT");
-    if (force && force[0] >= '0' && force[0] < '0' + kVariants) return launch_dim_any(a, force[0] - '0', st);
-    const std::pair<int, int> key{a.dim, efmax_of(a.ef)};
+    const int forced = forced_variant();
+    if (forced >= 0) return launch_dim_any(a, forced, st);
+    const TuneKey key{a.dim, efmax_of(a.ef), a.seed_mode};
     int var = -1;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tuned.find(key);
         if (it != g_tuned.end()) var = it->second;
     }
-    if (var >= 0 || a.nq < kTuneMin) return launch_dim_any(a, var >= 0 ? var : 0, st);
-    // every variant runs each slice; the slices' results are final
-    float total_ms[kVariants];
-    for (int v = 0; v < kVariants; ++v) total_ms[v] = 0.f;
+    if (var >= 0 || a.nq < kTuneChunks * kTuneMinChunk) return launch_dim_any(a, var >= 0 ? var : 0, st);
+    // NDC of each chunk: the caller's statistics counter, read around the chunk
+    static unsigned long long *own_stats[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    unsigned long long *cnt = a.stats;
+    if (!cnt) {
+        if (dev >= 64) return launch_dim_any(a, 0, st);
+        if (!own_stats[dev] && cudaMalloc(&own_stats[dev], 2 * sizeof(unsigned long long)) != cudaSuccess)
+            return launch_dim_any(a, 0, st);
+        cnt = own_stats[dev];
+    }
+    double ms_of[kVariants] = {}, ndc_of[kVariants] = {};
     cudaEvent_t e0, e1;
-    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    if (cudaEventCreate(&e0) != cudaSuccess) return launch_dim_any(a, 0, st);
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
         return launch_dim_any(a, 0, st);
+    }
     cudaError_t err = cudaSuccess;
-    int64_t pos = 0;
-    auto run_slice = [&](int v, int64_t len, bool timed) {
-        const SearchArgs sl = subrange(a, pos, pos + len);
-        err = cudaMemsetAsync(a.work, 0, sizeof(int32_t), st);  // each run starts its own count
-        if (err != cudaSuccess) return;
-        if (timed) cudaEventRecord(e0, st);
-        err = launch_dim_any(sl, v, st);
-        if (err != cudaSuccess || !timed) return;
-        cudaEventRecord(e1, st);
-        err = cudaEventSynchronize(e1);
+    unsigned long long before = 0, after = 0;
+    for (int c = 0; c < kTuneChunks && err == cudaSuccess; ++c) {
+        const int v = (c + c / kVariants) % kVariants;
+        SearchArgs sl = subrange(a, a.nq * c / kTuneChunks, a.nq * (c + 1) / kTuneChunks);
+        sl.stats = cnt;
+        err = cudaMemcpyAsync(&before, cnt, sizeof(before), cudaMemcpyDeviceToHost, st);
+        if (err == cudaSuccess) err = cudaMemsetAsync(a.work, 0, sizeof(int32_t), st);
+        if (err == cudaSuccess) err = cudaEventRecord(e0, st);
+        if (err == cudaSuccess) err = launch_dim_any(sl, v, st);
+        if (err == cudaSuccess) err = cudaEventRecord(e1, st);
+        if (err == cudaSuccess) err = cudaMemcpyAsync(&after, cnt, sizeof(after), cudaMemcpyDeviceToHost, st);
+        if (err == cudaSuccess) err = cudaStreamSynchronize(st);
         float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        total_ms[v] += ms;
-    };
-    for (int v = 0; v < kVariants && err == cudaSuccess; ++v) run_slice(v, kTuneWarm, false);
-    pos += kTuneWarm;
-    for (int rep = 0; rep < kTuneReps && err == cudaSuccess; ++rep) {
-        for (int k = 0; k < kVariants && err == cudaSuccess; ++k)
-            run_slice(rep % 2 == 0 ? k : kVariants - 1 - k, kTuneSlice, true);
-        pos += kTuneSlice;
+        if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+        ms_of[v] += ms;
+        ndc_of[v] += (double)(after - before);
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (err != cudaSuccess) return err;
     int best = 0;
     for (int v = 1; v < kVariants; ++v)
-        if (total_ms[v] < total_ms[best]) best = v;
-    {
-        std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tuned[key] = best;
-    }
-    err = cudaMemsetAsync(a.work, 0, sizeof(int32_t), st);
-    if (err != cudaSuccess) return err;
-    return launch_dim_any(subrange(a, pos, a.nq), best, st);
+        if (ms_of[v] * ndc_of[best] < ms_of[best] * ndc_of[v]) best = v;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned[key] = best;
+    return cudaSuccess;
 }
 
 bool search_dim_supported(int dim) {

@@ -8,7 +8,7 @@ it can compute one by one, and properties that hold at any size:
   out-degree <= R, rows of the source segment in (distance, id) order and
   obeying the occlusion rule (no kept s before c with alpha d(s,c) <= d(v,c)),
   with exact FP64 distances on sampled rows (integer data: FP32 is exact);
-* the beam search over the full target graph with 60,000 queries (the
+* the beam search over the full target graph with 70,000 queries (the
   autotuned launch shape): sampled queries equal the oracle's Algorithm 1 bit
   for bit;
 * the prune over 100,000 owners with pools of R + 32 candidates: sampled
@@ -79,7 +79,7 @@ def test_full_size_search_parity_sampled(rn, full):
     segs, vd, graphs, tsegs, out, st = full
     T, (gT, eT) = vd[0], graphs[0]
     rng = np.random.default_rng(1)
-    qi = rng.choice(len(segs[1]), 60_000, replace=False)
+    qi = rng.choice(len(segs[1]), 70_000, replace=False)
     Q = torch.from_numpy(segs[1][qi]).cuda()
     seeds = torch.full((len(qi), 1), eT, dtype=torch.int32, device="cuda")
     ids, dd, _ = rn.search(T, gT, Q, seeds, L, L)

@@ -447,12 +447,12 @@ def test_low_precision_merge_equals_fp32_embedding_shape(rn, prec):
 # ---------------------------------------------------------------- autotuner
 
 def test_search_variants_and_autotuned_launch_agree(rn, monkeypatch):
-    # 60k queries trigger the autotuner (slices run with different launch
-    # shapes, with and without the L2 prefetch); every variant must give the
-    # same results as the oracle.
+    # 66k queries trigger the autotuner (16 chunks of the launch run with
+    # different launch shapes, with and without the L2 prefetch); every variant
+    # must give the same results as the oracle.
     X = gen.sift_like(20000, 101, d=32)
     adj, ep = oracle.build_graph(X, 16, 32, 1.2)
-    Q = gen.sift_like(60000, 102, d=32)
+    Q = gen.sift_like(66000, 102, d=32)
     seeds = np.full((len(Q), 1), ep, np.int32)
     want, _, _, _, _ = oracle.beam_search(X, adj, Q, seeds, 24, 10)
     outs = []
@@ -468,7 +468,7 @@ def test_search_variants_and_autotuned_launch_agree(rn, monkeypatch):
 
 
 def test_expand_autotuned_on_large_batch(rn):
-    X = gen.sift_like(60000, 103, d=32)
+    X = gen.sift_like(66000, 103, d=32)
     adj, _ = oracle.build_graph(X, 16, 32, 1.2)
     want, _, _, _ = oracle.expand(X, adj, 12)
     got = rn.expand(dev(X), dev(adj), 12)
