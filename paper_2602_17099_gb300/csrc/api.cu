@@ -132,6 +132,7 @@ struct QuantBufs {
     void *q = nullptr;
     void *qlo = nullptr;   // two-term BF16 tiles of inner-product rows: the low terms
     float *scale = nullptr, *err = nullptr, *norm = nullptr;
+    int32_t pair_hi_only = 0;   // pair tile: exact hi terms (set by pair_exactness)
 };
 
 void take_quant(Bump &b, int64_t n, int32_t dim, int32_t prec, int32_t metric, QuantBufs &qb) {
@@ -161,6 +162,17 @@ void apply_quant(PruneArgs &a, const QuantBufs *qb, unsigned long long *rechecks
     a.qscale = qb->scale;
     a.qerr = qb->err;
     a.qnorm = qb->norm;
+    a.pair_hi_only = qb->pair_hi_only;
+}
+
+// The pair tile stages hi terms only when the rows are integers spanning at most
+// 256 (checked on the device once per call).
+rnsm_status pair_exactness(const SegTable &tab, int32_t dim, int32_t prec, int32_t metric,
+                           const Ctl &c, cudaStream_t st, QuantBufs &qb) {
+    qb.pair_hi_only = 0;
+    if (prec == 0 || !prune_pair_ok(dim, prec, metric)) return RNSM_OK;
+    CK(launch_pair_exact_check(tab, dim, c.work + 12, &qb.pair_hi_only, st));
+    return RNSM_OK;
 }
 
 constexpr int kWorkSlots = 16;
@@ -605,6 +617,7 @@ rnsm_status rnsm_prune(const float *vecs, int64_t n, int32_t dim, const int32_t 
     a.out_by_index = 1;
     a.err = c.err;
     if (qb.q) CK(launch_quantize(tab, n, dim, qprec, qb.q, qb.qlo, qb.scale, qb.err, qb.norm, st));
+    TRY(pair_exactness(tab, dim, qprec, metric, c, st, qb));
     apply_quant(a, &qb, c.rechecks);
     TRY(run_prune(a, c.work + 8, c, st));
     TRY(check_err_word(c, st));
@@ -1030,6 +1043,9 @@ rnsm_status rnsm_merge(const rnsm_segment *segs, int32_t m, const rnsm_params *p
     if (mb.qb.q)  // BF16 / E4M3 copies of every row for the one-term tensor-core tiles
         CK(launch_quantize(tab, off, dim, qprec, mb.qb.q, mb.qb.qlo, mb.qb.scale, mb.qb.err,
                            mb.qb.norm, st));
+    // (a captured graph keeps its launch arguments: the general pair tile there)
+    mb.qb.pair_hi_only = 0;
+    if (!(p.flags & RNSM_FLAG_GRAPH)) TRY(pair_exactness(tab, dim, qprec, p.metric, c, st, mb.qb));
     tm.end(t_init);
 
     const int32_t ks = p.ef_slide < p.L ? p.ef_slide : p.L;

@@ -122,6 +122,7 @@ struct PruneArgs {
     unsigned long long *ovf_count;
     int32_t *err;             // bit 4: pool larger than the capacity; bit 6: tile wait ran out
     int32_t test_withhold_commit;  // test-only (tensor-core prune): never signal MMA completion
+    int32_t pair_hi_only;     // pair tile: integer rows spanning <= 256, hi terms only
 };
 
 cudaError_t launch_prune(const PruneArgs &a, cudaStream_t st);
@@ -140,6 +141,10 @@ cudaError_t launch_prune_tc(const PruneArgs &a, cudaStream_t st, int terms = 0);
 bool prune_pair_ok(int dim, int prec, int metric);
 int prune_pair_max_pool();
 cudaError_t launch_prune_pair(const PruneArgs &a, cudaStream_t st);
+// *hi_only = 1 if every component of the table's rows is an integer and they span
+// at most 256 (scratch: 3 device ints; synchronises the stream).
+cudaError_t launch_pair_exact_check(const SegTable &t, int32_t dim, int32_t *scratch, int32_t *hi_only,
+                                    cudaStream_t st);
 // Rows of the segment table to BF16 (prec 1) or E4M3 with per-row scale (prec 2),
 // plus residual norms and row norms.
 // With q_lo (BF16 only) the rows are split into q = bf16(x) and q_lo = bf16(x - q)

@@ -48,6 +48,7 @@
 #include <stddef.h>
 #include <stdint.h>
 #include <stdlib.h>
+#include <string.h>
 
 #include "internal.h"
 #include "tcgen05.cuh"
@@ -115,6 +116,10 @@ __device__ __noinline__ int decide_open(float g, float gs, float ns2, float gc, 
     return (fmaf(alpha, d, -dvc) <= 0.f ? 1 : 0) | 2;
 }
 
+// kHiOnly: every component of every row is an integer and their range is at
+// most 256 (checked on the device before the launch), so y = x_c - x_v is exact
+// in FP32 and in BF16: the tile holds hi only (half the shared memory).
+template <bool kHiOnly>
 __global__ void __launch_bounds__(kQT) prune_pair_kernel(const PruneArgs a, int chunk) {
     extern __shared__ __align__(1024) unsigned char tile[];
     __shared__ PairSmem s;
@@ -229,7 +234,8 @@ __global__ void __launch_bounds__(kQT) prune_pair_kernel(const PruneArgs a, int 
             if (!valid_t) {
                 for (int u = 0; u < U; ++u) {
                     *reinterpret_cast<uint4 *>(hrow + u * 128) = make_uint4(0u, 0u, 0u, 0u);
-                    *reinterpret_cast<uint4 *>(hrow + region + u * 128) = make_uint4(0u, 0u, 0u, 0u);
+                    if (!kHiOnly)
+                        *reinterpret_cast<uint4 *>(hrow + region + u * 128) = make_uint4(0u, 0u, 0u, 0u);
                 }
             } else {
                 // the FP32 prune distance, chains E (even dimensions) and O (odd) over
@@ -264,21 +270,27 @@ __global__ void __launch_bounds__(kQT) prune_pair_kernel(const PruneArgs a, int 
                             float y0, y1;
                             f2_split(y, y0, y1);
                             const __nv_bfloat162 hb = __floats2bfloat162_rn(y0, y1);
-                            const float2 hf = __bfloat1622float2(hb);
-                            // y - hi is exact in FP32
-                            float t0, t1;
-                            f2_split(f2_sub(y, f2_of(hf.x, hf.y)), t0, t1);
-                            const __nv_bfloat162 lb = __floats2bfloat162_rn(t0, t1);
                             hw[e] = *reinterpret_cast<const uint32_t *>(&hb);
-                            lw[e] = *reinterpret_cast<const uint32_t *>(&lb);
+                            lw[e] = 0u;
+                            if (!kHiOnly) {
+                                const float2 hf = __bfloat1622float2(hb);
+                                // y - hi is exact in FP32
+                                float t0, t1;
+                                f2_split(f2_sub(y, f2_of(hf.x, hf.y)), t0, t1);
+                                const __nv_bfloat162 lb = __floats2bfloat162_rn(t0, t1);
+                                lw[e] = *reinterpret_cast<const uint32_t *>(&lb);
+                            }
                         }
                         if (whole) {   // no tests: the tile rows stay zero
                             hw[0] = hw[1] = hw[2] = hw[3] = 0u;
                             lw[0] = lw[1] = lw[2] = lw[3] = 0u;
                         }
-                        lo_any |= ((lw[0] | lw[1] | lw[2] | lw[3]) & 0x7fff7fffu) != 0u;
                         *reinterpret_cast<uint4 *>(hrow + u * 128) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-                        *reinterpret_cast<uint4 *>(hrow + region + u * 128) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                        if (!kHiOnly) {
+                            lo_any |= ((lw[0] | lw[1] | lw[2] | lw[3]) & 0x7fff7fffu) != 0u;
+                            *reinterpret_cast<uint4 *>(hrow + region + u * 128) =
+                                make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                        }
                     }
                 }
                 dxt = chain2_final(acc, 0);
@@ -533,7 +545,74 @@ __global__ void __launch_bounds__(kQT) prune_pair_kernel(const PruneArgs a, int 
     if (warp == 0) tc::tmem_dealloc(taddr, kQCols);
 }
 
+// Order-preserving int image of a float (for atomicMin / atomicMax).
+__device__ __forceinline__ int ordered(float f) {
+    const int b = __float_as_int(f);
+    return b >= 0 ? b : b ^ 0x7fffffff;
+}
+
+// out[0] |= 1 if a component is not an integer; out[1] / out[2]: min / max
+// component (ordered ints).  blockIdx.y = segment.
+__global__ void exact_range_kernel(SegTable t, int dim, int *out) {
+    const int seg = blockIdx.y;
+    const int64_t n4 = (t.off[seg + 1] - t.off[seg]) * dim / 4;
+    const float4 *x = reinterpret_cast<const float4 *>(t.base[seg]);
+    int nonint = 0;
+    float lo = INFINITY, hi = -INFINITY;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float4 v = x[i];
+        const float c[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            nonint |= !(c[k] == rintf(c[k]));
+            lo = fminf(lo, c[k]);
+            hi = fmaxf(hi, c[k]);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        nonint |= __shfl_xor_sync(0xffffffffu, nonint, o);
+        lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (nonint) atomicOr(&out[0], 1);
+        atomicMin(&out[1], ordered(lo));
+        atomicMax(&out[2], ordered(hi));
+    }
+}
+
+float from_ordered(int b) {
+    const int v = b >= 0 ? b : b ^ 0x7fffffff;
+    float f;
+    memcpy(&f, &v, sizeof(f));
+    return f;
+}
+
 }  // namespace
+
+cudaError_t launch_pair_exact_check(const SegTable &t, int32_t dim, int32_t *scratch, int32_t *hi_only,
+                                    cudaStream_t st) {
+    *hi_only = 0;
+    if (t.m <= 0 || t.off[t.m] <= 0) return cudaSuccess;
+    int init[3] = {0, 0x7fffffff, (int)0x80000000};
+    cudaError_t e = cudaMemcpyAsync(scratch, init, sizeof(init), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return e;
+    exact_range_kernel<<<dim3(256, (unsigned)t.m), 256, 0, st>>>(t, dim, scratch);
+    note_launches(1);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    int res[3];
+    e = cudaMemcpyAsync(res, scratch, sizeof(res), cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return e;
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return e;
+    // integers spanning at most 256: every difference of two components is an
+    // integer of magnitude <= 256, exact in FP32 and in BF16 (8 significant bits)
+    *hi_only = res[0] == 0 && (double)from_ordered(res[2]) - (double)from_ordered(res[1]) <= 256.0;
+    return cudaSuccess;
+}
 
 bool prune_pair_ok(int dim, int prec, int metric) {
     return prec == 1 && metric == 0 && dim >= 16 && dim <= kQMaxDim && dim % 16 == 0;
@@ -546,8 +625,9 @@ cudaError_t launch_prune_pair(const PruneArgs &in, cudaStream_t st) {
     PruneArgs a = in;
     // test-only: withhold the MMA completion signal, so every wait runs out
     a.test_withhold_commit = getenv("RNSM_TEST_WITHHOLD_COMMIT") != nullptr;
-    const size_t dyn = (size_t)512 * a.dim;   // hi and lo terms, 128 rows of 2 dim bytes each
-    auto kern = prune_pair_kernel;
+    // hi (and lo) terms, 128 rows of 2 dim bytes each
+    const size_t dyn = (size_t)(a.pair_hi_only ? 256 : 512) * a.dim;
+    auto kern = a.pair_hi_only ? prune_pair_kernel<true> : prune_pair_kernel<false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     if (e != cudaSuccess) return e;
     cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);

@@ -387,13 +387,17 @@ def test_merge_host_and_device_pivots_agree(rn):
     # BF16 at L2 and d <= 128 with pools <= 64: two owners per tile (real-valued
     # rows need the lo term, integer rows do not); R = pool size; d = 16
     ("deepl2", 96, 64, 32), ("deepl2", 96, 40, 16), ("deepl2", 128, 64, 64),
-    ("gauss", 16, 64, 32), ("gauss", 64, 33, 8), ("sift", 48, 64, 32)])
+    ("gauss", 16, 64, 32), ("gauss", 64, 33, 8), ("sift", 48, 64, 32),
+    # integer rows spanning <= 256 (far from 0): hi terms only; spanning 510: hi and lo
+    ("offset", 128, 64, 32), ("wide", 128, 64, 32)])
 def test_low_precision_prune_equals_fp32(rn, prec, kind, d, w, R):
     n = 3000
     X = {"gauss": lambda: gen.gaussian(n, d, 90),
          "deep": lambda: gen.deep_like(n, 91, d=d),
          "deepl2": lambda: gen.deep_like(n, 94, d=d),
          "sift": lambda: gen.sift_like(n, 92, d=d),
+         "offset": lambda: gen.sift_like(n, 92, d=d) + np.float32(1000.0),
+         "wide": lambda: gen.sift_like(n, 92, d=d) * np.float32(2.0),
          "embed": lambda: gen.embed_like(n, 93, d=d, n_comp=50)}[kind]()
     metric = oracle.IP if kind in ("deep", "embed") else oracle.L2
     owners, pool = _pools(n, w, 7 * d + w, 800)
