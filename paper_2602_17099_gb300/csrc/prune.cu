@@ -77,27 +77,27 @@ __device__ __forceinline__ void carve(unsigned char *p, int rows_cap, int pool_c
 
 
 // Stages float4 columns [d0/4, d0/4 + dc4) of rows [0, nrows4) (rptr) into
-// smem; eight loads are issued before their stores so they overlap.
-template <int NT>
+// smem; U loads per thread are issued before their stores so they overlap.
+template <int NT, int U = 8>
 __device__ __forceinline__ void stage_rows(float4 *rows, const float *const *rptr, int nrows4,
                                            int d0, int dc4) {
-    const int total = nrows4 * dc4;
-    for (int e0 = threadIdx.x; e0 < total; e0 += 8 * NT) {
-        float4 v[8];
+    // a warp per row, a lane per float4: coalesced 512-byte row reads, conflict-free
+    // stores, U rows in flight per warp, no index division
+    constexpr int NW = NT / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int f = lane; f - lane < dc4; f += 32) {
+        const bool fin = f < dc4;
+        for (int r0 = warp; r0 < nrows4; r0 += U * NW) {
+            float4 v[U];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int e = e0 + u * NT;
-            if (e < total) {
-                const int r = e / dc4, f = e - r * dc4;
-                v[u] = ldg4(rptr[r] + d0 + 4 * f);
+            for (int u = 0; u < U; ++u) {
+                const int r = r0 + u * NW;
+                if (fin && r < nrows4) v[u] = ldg4(rptr[r] + d0 + 4 * f);
             }
-        }
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int e = e0 + u * NT;
-            if (e < total) {
-                const int r = e / dc4, f = e - r * dc4;
-                rows[srow4(r) + f] = v[u];
+            for (int u = 0; u < U; ++u) {
+                const int r = r0 + u * NW;
+                if (fin && r < nrows4) rows[srow4(r) + f] = v[u];
             }
         }
     }
@@ -490,6 +490,11 @@ struct SmallSmem {
 #ifndef RNSM_SMALL_MIN_BLOCKS
 #define RNSM_SMALL_MIN_BLOCKS 4   // resident CTAs per SM the register budget is cut for
 #endif
+// rows in flight per warp while the small-pool kernel stages its rows (more in
+// flight spill registers of the 96 it has at four CTAs per SM)
+#ifndef RNSM_SMALL_STAGE_UNROLL
+#define RNSM_SMALL_STAGE_UNROLL 4
+#endif
 __global__ void __launch_bounds__(kSmallThreads, RNSM_SMALL_MIN_BLOCKS) prune_small_kernel(const PruneArgs a, int chunk) {
     __shared__ __align__(16) SmallSmem s;
     __shared__ int64_t sh_i;
@@ -564,7 +569,7 @@ __global__ void __launch_bounds__(kSmallThreads, RNSM_SMALL_MIN_BLOCKS) prune_sm
                 for (int q = 0; q < 4; ++q) acc[t][p][q] = 0ull;
         for (int d0 = 0; d0 < dim; d0 += kDch) {
             const int dc4 = min(kDch, dim - d0) >> 2;
-            stage_rows<kSmallThreads>(s.rows, s.rptr, 4 * nB, d0, dc4);
+            stage_rows<kSmallThreads, RNSM_SMALL_STAGE_UNROLL>(s.rows, s.rptr, 4 * nB, d0, dc4);
             __syncthreads();
 #pragma unroll
             for (int t = 0; t < kSmallNB; ++t) {
