@@ -58,7 +58,9 @@ typedef enum {
 typedef enum { RNSM_METRIC_L2 = 0, RNSM_METRIC_IP = 1 } rnsm_metric;
 
 /* Arithmetic of the candidate-by-candidate prune tiles (Section 4.2,
- * UpdateGraph).  Searches always run in FP32. */
+ * UpdateGraph).  Searches always run in FP32.  BF16 and FP8 tiles run on the
+ * tensor cores and every decision a tile cannot settle within its error bound
+ * is re-decided with the FP32 distance, so the result equals the FP32 one. */
 typedef enum { RNSM_PREC_FP32 = 0, RNSM_PREC_BF16 = 1, RNSM_PREC_FP8 = 2 } rnsm_precision;
 
 /* One input segment: a vector set X_i and its proximity graph G_i
