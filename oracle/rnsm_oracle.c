@@ -17,7 +17,7 @@
  *     target vertices gain cross edges only via reverse edges).
  *   - MOS: Algorithm 3 (Section 5) and the execution order of its edges.
  *
- * Readings where the paper is silent (listed in the design doc as well):
+ * Readings where the paper is silent:
  *   - candidate order is lexicographic on (distance, id); ties go to the
  *     lower id everywhere;
  *   - "each unexpanded neighbour" of Algorithm 1 is read as "each neighbour
