@@ -106,10 +106,12 @@ cudaError_t launch_locality_order(const float *x, int64_t n, int32_t dim, int32_
                                   size_t scan_tmp_bytes, int32_t *order, int32_t *rank,
                                   cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
-    // about eight vertices per key at least, at most 2^12 keys
-    int nb = 1;
+    // about eight vertices per key at least, at most 2^12 keys; a single key below
+    // 16 vertices (the counting-sort scratch holds as many keys as the largest
+    // segment has vertices)
+    int nb = 0;
     while (nb < kMaxPlanes && ((int64_t)8 << (nb + 1)) <= n) ++nb;
-    const size_t smem = sizeof(float) * ((size_t)nb * dim + nb);
+    const size_t smem = sizeof(float) * ((size_t)nb * dim + nb + 1);
     cudaError_t e = cudaFuncSetAttribute(lsh_key_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;

@@ -246,6 +246,20 @@ def test_merge_multi_segment_plan_exact(rn):
     np.testing.assert_array_equal(got, want)
 
 
+def test_merge_tiny_segments_exact(rn):
+    # segments of 1, 9 and 15 vertices (fewer than the query schedule's smallest
+    # locality bucket, one vertex without edges), in FP32 and BF16
+    sizes = [1, 9, 15]
+    segs = [gen.sift_like(n, 70 + i, d=32) for i, n in enumerate(sizes)]
+    gs = [oracle.build_graph(s, 4, 8, 1.2) for s in segs]
+    plan = [(1, 0), (0, 2), (1, 2)]
+    want, _ = oracle.rnsm_merge(segs, [g for g, _ in gs], [e for _, e in gs], plan, 4, 8, 1.2)
+    tsegs = [(dev(sg), dev(g), e) for sg, (g, e) in zip(segs, gs)]
+    for prec in (rn.FP32, rn.BF16):
+        got, _ = rn.merge(tsegs, rn.params(4, 8, 1.2, prec=prec), [(a, b, 0.0) for a, b in plan])
+        np.testing.assert_array_equal(host(got), want)
+
+
 @pytest.mark.parametrize("flags", [0, 2])
 def test_merge_batched_plan_with_shared_sources_exact(rn, flags):
     # six uneven segments, a hand-made plan where sources serve several edges and
