@@ -473,10 +473,14 @@ __global__ void __launch_bounds__(kThreads) prune_kernel(const PruneArgs a, int 
 constexpr int kSmallThreads = 160;    // one 4x4 block of the triangle per thread
 constexpr int kSmallMax = 64;
 constexpr int kSmallRows = 68;      // owner + 64, rounded up to 4
+// distances of the (owner + pool) rows as a symmetric square matrix in the row
+// buffer, row stride odd so a column read by 32 lanes hits 32 banks
+constexpr int kSmallTs = 69;
+static_assert(rows_float4(kSmallRows) * 4 >= (kSmallMax + 1) * kSmallTs, "matrix fits the row buffer");
 constexpr int kSmallNB = 1;         // 17*18/2 = 153 blocks over 160 threads
 
 struct SmallSmem {
-    float4 rows[rows_float4(kSmallRows)];
+    float4 rows[rows_float4(kSmallRows)];   // staged rows, then the distance matrix
     const float *rptr[kSmallRows];
     int32_t pid[kSmallMax];
     float kd[kSmallMax];       // raw keys
@@ -601,7 +605,11 @@ __global__ void __launch_bounds__(kSmallThreads, RNSM_SMALL_MIN_BLOCKS) prune_sm
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     const int ra = 4 * bas[t] + p, rb = 4 * bbs[t] + q;
-                    if (ra < rb && rb < nrows) T[tri(ra, rb, nrows)] = chain2_final(acc[t][p][q], metric);
+                    if (ra < rb && rb < nrows) {   // symmetric square layout
+                        const float dv = chain2_final(acc[t][p][q], metric);
+                        T[ra * kSmallTs + rb] = dv;
+                        T[rb * kSmallTs + ra] = dv;
+                    }
                 }
         }
         __syncthreads();
@@ -611,7 +619,7 @@ __global__ void __launch_bounds__(kSmallThreads, RNSM_SMALL_MIN_BLOCKS) prune_sm
         // next to each other; -1 and the owner sort last.
         for (int j = tid; j < kSmallMax; j += kSmallThreads) {
             const bool valid = j < nr && s.pid[j] >= 0;
-            s.kd[j] = valid ? T[tri(0, 1 + j, nrows)] : INFINITY;
+            s.kd[j] = valid ? T[1 + j] : INFINITY;
             s.kix[j] = valid ? s.pid[j] : INT32_MAX;
         }
         __syncthreads();
@@ -637,13 +645,11 @@ __global__ void __launch_bounds__(kSmallThreads, RNSM_SMALL_MIN_BLOCKS) prune_sm
             bool t0 = false, t1 = false;
             if (lane < c) {
                 const int sr = s.srow[lane];
-                const float dsc = sr < cr ? T[tri(sr, cr, nrows)] : T[tri(cr, sr, nrows)];
-                t0 = fmaf(a.alpha, dsc, -dvc) <= 0.f;
+                t0 = fmaf(a.alpha, T[sr * kSmallTs + cr], -dvc) <= 0.f;
             }
             if (lane + 32 < c) {
                 const int sr = s.srow[lane + 32];
-                const float dsc = sr < cr ? T[tri(sr, cr, nrows)] : T[tri(cr, sr, nrows)];
-                t1 = fmaf(a.alpha, dsc, -dvc) <= 0.f;
+                t1 = fmaf(a.alpha, T[sr * kSmallTs + cr], -dvc) <= 0.f;
             }
             const unsigned m0 = __ballot_sync(0xffffffffu, t0);
             const unsigned m1 = __ballot_sync(0xffffffffu, t1);
