@@ -817,7 +817,6 @@ int32_t orc_rnsm_merge(const float *X, int64_t d, const int64_t *seg_off, int32_
         ef_slide < 1 || ef_slide > L || c_cross < 1 || c_cross > ef_slide)
         return ORC_EINVAL;
     set_threads(nthreads);
-    int64_t N = seg_off[m];
     int64_t st[8] = {0};
     /* initial merged lists: input lists in global ids */
     for (int32_t s = 0; s < m; ++s)
