@@ -54,3 +54,22 @@ def test_single_rank_needs_no_process_group():
     assert bench.init_dist(1) is None
     assert bench.allmax(None, 3.5) == 3.5
     assert bench.whole_job_rate(10, 2, 1, 1000.0) == 20.0
+
+
+def test_profile_traffic_only_for_matching_sources(tmp_path):
+    # the committed ncu summaries give per-launch DRAM bytes only while the
+    # kernel sources they were taken on are unchanged (sha256 prefix)
+    import hashlib
+    sys.path.insert(0, ROOT)
+    import bench
+    src = tmp_path / "k.cu"
+    src.write_bytes(b"__global__ void k() {}\n")
+    h = hashlib.sha256(src.read_bytes()).hexdigest()[:16]
+    prof = tmp_path / "p.txt"
+    prof.write_text(f"# title\n\nsources sha256[:16]: {h}\nbytes per launch: 123456\n")
+    assert bench.profile_traffic(str(prof), [str(src)], "sources sha256[:16]",
+                                 "bytes per launch") == 123456.0
+    src.write_bytes(b"__global__ void k() { }\n")          # the kernel changed
+    assert bench.profile_traffic(str(prof), [str(src)], "sources sha256[:16]",
+                                 "bytes per launch") is None
+    assert bench.profile_traffic(str(tmp_path / "none.txt"), [str(src)], "a", "b") is None
