@@ -7,30 +7,36 @@
 // kernel packs two owners into one 128 x 128 Gram tile and keeps every phase
 // inside the two warps that own the candidates' TMEM lanes:
 //
-//  1. Owner distances, exact.  Each thread takes one pool slot and computes
-//     d(v, c) with the FP32 prune distance (the two-chain definition of
-//     common.cuh), so the (distance, id) order is the FP32 order without any
-//     interval logic; the slots are ranked by counting.
-//  2. Staging, in that order.  The thread of position p reads its candidate's
-//     FP32 row again, centres it on the owner (y = x_c - x_v, rounded once),
-//     splits y into hi = bf16(y) and lo = bf16(y - hi) and writes both into
-//     the K-major no-swizzle tile: rows 0..63 are owner A's positions, rows
-//     64..127 owner B's.  If every lo of the pair is zero (integer-valued
-//     data), only hi is used.
+//  1. Pool.  Slot t of owner o gets its id; a repeated id keeps its first slot
+//     (match_any in a warp, a 32-entry scan across the two warps), so the
+//     remaining (distance, id) keys are distinct.
+//  2. One pass per row, in slot order.  The slot's thread reads its FP32 row
+//     once: v - x feeds the two chains of the FP32 prune distance (the
+//     definition of common.cuh), giving the exact owner distance, and the same
+//     v - x (the row centred on the owner, rounded once) is split into
+//     hi = bf16(y) and lo = bf16(y - hi) and written into the K-major
+//     no-swizzle tile: rows 0..63 are owner A's slots, rows 64..127 owner B's.
+//     If every lo of the pair is zero only hi.hi is multiplied; when the whole
+//     table is integer-valued with a range of at most 256 the kernel is
+//     instantiated without lo terms at all (kHiOnly).
 //  3. One thread issues the MMAs (hi.hi, plus lo.hi, hi.lo and lo.lo) of the
 //     tile against itself, M = N = 128, into 128 TMEM columns, and commits
-//     them to an mbarrier (every wait bounded by 1 s).
-//  4. Warp w reads TMEM lanes 32w..32w+31, i.e. 32 positions s of one owner,
-//     and that owner's 64 columns c.  From the centred Gram G:
+//     them to an mbarrier (the wait is bounded by 1 s).  Meanwhile every slot
+//     builds the mask of the slots before it in (distance, id) order: the
+//     order is exact, so no owner-distance interval logic is needed.
+//  4. Warp w reads TMEM lanes 32w..32w+31, i.e. 32 slots s of one owner, and
+//     that owner's 64 columns c.  From the centred Gram G:
 //     d~(s, c) = G_ss + G_cc - 2 G_sc, with |d~ - d_fp32(s, c)| <=
 //     kappa (n_s + n_c)^2 <= b_s + b_c, n_r^2 a bound on the squared norm of
 //     the staged row r (from G_rr).  A test "s occludes c" (s before c) is
 //     settled by the tile when alpha (d~ +- (b_s + b_c)) - d(v, c) has one
 //     sign, else by a tighter per-pair bound, else by the exact FP32
 //     distance with the FP32 prune's own rule fmaf(alpha, d, -d(v, c)) <= 0.
-//     The ballots of a column are the occluder bits of c by position.
-//  5. One warp per owner runs the greedy walk in ballot rounds (as the FP32
-//     small-pool kernel) and writes the kept ids.
+//     The ballots of a column are the occluder bits of c by slot.
+//  5. One warp per owner runs the greedy walk in ballot rounds on slot masks
+//     (as the FP32 small-pool kernel does on positions); a kept slot's output
+//     index is the number of kept slots before it, and the cap keeps the
+//     first R.  The other warp prefetches the next owner's rows into L2.
 //
 // The result equals the FP32 prune's: the order is exact, and every
 // occlusion decision either follows from a proven bound or is taken in FP32.
