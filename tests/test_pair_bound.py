@@ -1,4 +1,5 @@
-"""The error bound of the BF16 pair tile, checked by emulation on the CPU.
+"""The error bounds of the tensor-core prune tiles, checked by emulation on
+the CPU (the BF16 pair tile at L2; the general tile's inner-product rows).
 
 The pair tile decides an occlusion test from the tile only when the tile's
 distance d~(s, c) = G_ss + G_cc - 2 G_sc is within kappa (n_s + n_c)^2 of the
@@ -106,3 +107,48 @@ def test_integer_rows_spanning_256_need_no_lo_term():
     assert np.array_equal(bf16_rn(y), y)
     # one step past the range is no longer exact
     assert bf16_rn(np.float32(257.0)) != np.float32(257.0)
+
+
+def ip_chain(a, b):
+    """The FP32 prune distance for inner product: two chains of fma(a_k, b_k),
+    then 1 - (E + O)."""
+    e = np.zeros((len(a), len(b)), np.float32)
+    o = np.zeros((len(a), len(b)), np.float32)
+    for k in range(0, a.shape[1], 2):
+        e = fma32(a[:, None, k], b[None, :, k], e)
+        o = fma32(a[:, None, k + 1], b[None, :, k + 1], o)
+    return (np.float32(1.0) - (e + o)).astype(np.float32)
+
+
+@pytest.mark.parametrize("d,terms", [(768, 2), (256, 1)])
+def test_general_tile_inner_product_bound(d, terms):
+    # the general tile's inner-product rows: stored hi (and lo) terms, residual
+    # norm E = ||x - hi - lo|| (rounded up), row norm ||x||; the Gram of the
+    # staged terms in FP32 steps of 16 products; bound of the kernel:
+    #   1.01 (n_s E_c + E_s n_c + E_s E_c + eps_c (n_s + E_s)(n_c + E_c) + gam n_s n_c + 2^-23)
+    X = gen.embed_like(64 * 4, 16, d=d, n_comp=8).astype(np.float32)
+    hi = bf16_rn(X)
+    lo = bf16_rn((X - hi).astype(np.float32)) if terms == 2 else np.zeros_like(X)
+    res = (X.astype(np.float64) - hi - lo)
+    E = np.sqrt((res ** 2).sum(1)) * 1.001 + 1e-30
+    nrm = np.sqrt((X.astype(np.float64) ** 2).sum(1)) * 1.0001
+    x = hi.astype(np.float64) + lo.astype(np.float64)
+    n_instr = (4 if terms == 2 else 1) * (d // 16)
+    eps_c = 1.01 * (n_instr + 1) * 2.0 ** -22
+    gam = 1.01 * (d + 2) * 2.0 ** -24
+    worst = 0.0
+    for g in range(0, len(X), 64):
+        idx = slice(g, g + 64)
+        G = np.zeros((64, 64), np.float32)
+        for k0 in range(0, d, 16):
+            G = (G.astype(np.float64) + x[idx, k0:k0 + 16] @ x[idx, k0:k0 + 16].T).astype(np.float32)
+        dt = 1.0 - G.astype(np.float64)
+        d32 = ip_chain(X[idx], X[idx]).astype(np.float64)
+        ns, es = nrm[idx], E[idx]
+        B = 1.01 * (ns[:, None] * es[None, :] + es[:, None] * ns[None, :] + es[:, None] * es[None, :]
+                    + eps_c * (ns[:, None] + es[:, None]) * (ns[None, :] + es[None, :])
+                    + gam * ns[:, None] * ns[None, :] + 1.2e-7)
+        err = np.abs(dt - d32)
+        assert (err <= B).all(), (d, terms, g)
+        worst = max(worst, float((err / B).max()))
+    assert worst < 1.0
