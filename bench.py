@@ -91,6 +91,16 @@ def _deep50(scale, nq):
     return gen.deep_like_gpu_segments(total, nq, 9, sizes, 1009, device=dev)
 
 
+def _incremental(scale, nq):
+    """10 partitions of a DEEP-like stream in arrival order (1M rows each at full
+    size), drawn on the GPU; merged one at a time into a growing index."""
+    import torch
+    n_part = max(20_000, int(1_000_000 * scale))
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    return gen.deep_like_gpu_segments(10 * n_part, nq, 11, [n_part] * 10, 0, device=dev,
+                                      stream=True, return_all=True)
+
+
 WORKLOADS = {
     "sift2x500k": Workload("sift2x500k", "sift-like 2x500k d128 L2 R32 L64 alpha1.2", 128, 32, 64,
                            1.2, L2_METRIC, _sift, False, ("bf16", "fp8"), 0.1),
@@ -103,6 +113,9 @@ WORKLOADS = {
     "deep50x100m": Workload("deep50x100m", "deep-like 50 segments (lognormal 0.5M-5M, 100M total, "
                             "cluster partition, drawn on the GPU) d96 L2 R32 L64 alpha1.2, MOS plan",
                             96, 32, 64, 1.2, L2_METRIC, _deep50, True, ("bf16",), 0.01),
+    "incr10x1m": Workload("incr10x1m", "deep-like stream d96 L2 R32 L64 alpha1.2: 10 partitions of "
+                          "1M in arrival order, each merged into the growing index (9 merges)",
+                          96, 32, 64, 1.2, L2_METRIC, _incremental, False, ("bf16",), 0.0),
 }
 
 
@@ -690,6 +703,112 @@ def run_ours(args, ws, rank, local):
     return 0
 
 
+def run_incremental(args, ws, rank, local):
+    """Incremental merging: partition 0's graph is the index; partitions 1..9 are
+    merged into it one at a time (each merge: the new partition is the source,
+    the index the target).  One step = the whole sequence of nine merges; value =
+    vertices of the merged graphs per second (sum over the nine merges)."""
+    import torch
+
+    from paper_2602_17099_gb300 import build as pkg_build
+    from paper_2602_17099_gb300 import rnsm as rn
+
+    W = WORKLOADS[args.workload]
+    dist = init_dist(ws)
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device (there is no CPU path)")
+    torch.cuda.set_device(local)
+    if rank == 0 or ws == 1:
+        pkg_build.build()
+    barrier(dist)
+    rn.lib()
+    segs, Q, allx = W.make(args.scale, args.recall_queries)
+    m, n_part = len(segs), len(segs[0])
+    progress(f"{W.name}: {m} partitions of {n_part} rows on the device")
+    t0 = time.perf_counter()
+    graphs = [rn.build_segment(v, W.R, W.L, W.alpha, metric=W.metric) for v in segs]
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    progress(f"partition graphs built in {build_s:.1f} s")
+    bufs = [torch.empty((m * n_part, W.R), dtype=torch.int32, device="cuda") for _ in range(2)]
+
+    def sequence(p):
+        g, e = graphs[0]
+        n_idx, stats = n_part, []
+        for k in range(1, m):
+            out = bufs[k % 2][:n_idx + n_part]
+            g, st = rn.merge([(allx[:n_idx], g, e), (segs[k], graphs[k][0], graphs[k][1])], p,
+                             plan=[(1, 0, 0.0)], out=out)
+            stats.append(st)
+            n_idx += n_part
+        return g, e, stats
+
+    units = sum((k + 1) * n_part for k in range(1, m))   # vertices of the nine merged graphs
+    p = rn.params(W.R, W.L, W.alpha, metric=W.metric)
+    for _ in range(args.warmup):
+        sequence(p)
+    torch.cuda.synchronize()
+    gpu_id = torch.cuda.get_device_properties(local).uuid
+    gpu_id = f"GPU-{gpu_id}" if not str(gpu_id).startswith("GPU-") else str(gpu_id)
+    sampler = ClockSampler(gpu_id)
+    time.sleep(0.5)
+    barrier(dist)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        final, entry, stats = sequence(p)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(dist)
+    clocks = sampler.stop()
+    ms = allmax(dist, ev0.elapsed_time(ev1))
+    value = whole_job_rate(units, args.steps, ws, ms)
+    progress(f"timed sequences: {ms / args.steps:.1f} ms each")
+    per_merge = [round(sum(st["phase_ms"]), 3) for st in stats]
+    launches = sum(st["launches"] for st in stats) * args.steps
+    ref = final.clone()
+    modes = {}
+    for name in W.modes:
+        prec = {"bf16": rn.BF16, "fp8": rn.FP8}[name]
+        pq = rn.params(W.R, W.L, W.alpha, metric=W.metric, prec=prec)
+        sequence(pq)
+        torch.cuda.synchronize()
+        q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        q0.record(stream)
+        fq, _, sq = sequence(pq)
+        q1.record(stream)
+        torch.cuda.synchronize()
+        qms = q0.elapsed_time(q1)
+        modes[name] = {"ms_per_step": qms, "value": units / (qms / 1000.0), "unit": UNIT,
+                       "identical_to_fp32": bool(torch.equal(fq, ref)),
+                       "rechecks_per_step": int(sum(st["rechecks"] for st in sq))}
+    rec = None
+    if args.recall_queries > 0:
+        rec = recall_at_10(rn, torch, W, allx, ref, entry, Q[:args.recall_queries])
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic (seeded; no dataset)",
+                "config": {"workload": W.desc, "partitions": m, "rows_per_partition": n_part,
+                           "dim": W.dim, "R": W.R, "L": W.L, "alpha": W.alpha, "metric": "l2",
+                           "precision": "fp32", "parallelism": "replicas" if ws > 1 else "single",
+                           "l2": "inputs larger than L2 (%d MB of vectors)" % (allx.numel() * 4 >> 20),
+                           "partition_graph_build_s": round(build_s, 3),
+                           "merge_ms_by_index_size": per_merge, "recall_at_10": rec},
+                "clocks": clocks, "gpu_launches": int(launches),
+                "e2e": {"value": None, "unit": UNIT,
+                        "skipped": "device-resident stream; the default workload carries e2e"},
+                "precision_modes": modes, "roofline": None, "cpu_baseline": None}
+        print(json.dumps(line), flush=True)
+    barrier(dist)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -708,7 +827,15 @@ def main():
         args.warmup = 3
     ws, rank, local = dist_env()
     if args.impl == "reference":
+        if args.workload == "incr10x1m":
+            if rank == 0:
+                print(json.dumps({"impl": "reference", "unavailable": "the incremental workload has "
+                                  "no oracle arm (its sequence is checked against the oracle in "
+                                  "tests/test_gpu_parity.py)"}), flush=True)
+            return 0
         return run_reference(args, ws, rank)
+    if args.workload == "incr10x1m":
+        return run_incremental(args, ws, rank, local)
     return run_ours(args, ws, rank, local)
 
 

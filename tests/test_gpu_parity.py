@@ -246,6 +246,23 @@ def test_merge_multi_segment_plan_exact(rn):
     np.testing.assert_array_equal(got, want)
 
 
+def test_incremental_merge_matches_oracle_step_by_step(rn):
+    # incremental merging (Exp-5's scenario): partition 0's graph is the index;
+    # every next partition is merged into it as the source, and the merged graph
+    # (global ids = index ids, then the partition's) is the next step's index
+    parts = [gen.sift_like(n, 80 + i, d=32) for i, n in enumerate([700, 500, 650, 400])]
+    gs = [oracle.build_graph(s, 12, 24, 1.2) for s in parts]
+    idx_x, (idx_g, idx_e) = parts[0], gs[0]
+    d_idx_g = dev(idx_g)
+    for k in range(1, len(parts)):
+        want, _ = oracle.rnsm_merge([idx_x, parts[k]], [idx_g, gs[k][0]], [idx_e, gs[k][1]],
+                                    [(1, 0)], 12, 24, 1.2)
+        got, _ = rn.merge([(dev(idx_x), d_idx_g, idx_e), (dev(parts[k]), dev(gs[k][0]), gs[k][1])],
+                          rn.params(12, 24, 1.2), [(1, 0, 0.0)])
+        np.testing.assert_array_equal(host(got), want)
+        idx_x, idx_g, d_idx_g = np.concatenate([idx_x, parts[k]]), want, got
+
+
 def test_merge_tiny_segments_exact(rn):
     # segments of 1, 9 and 15 vertices (fewer than the query schedule's smallest
     # locality bucket, one vertex without edges), in FP32 and BF16

@@ -117,14 +117,18 @@ def deep_like(n: int, seed: int, d: int = 96, n_comp: int = 1000, rank: int = 32
 
 def deep_like_gpu_segments(n: int, nq: int, seed: int, sizes, part_seed: int, device="cuda",
                            d: int = 96, n_comp: int = 1000, rank: int = 32, scale: float = 0.06,
-                           noise: float = 0.01, chunk: int = 1 << 15):
+                           noise: float = 0.01, chunk: int = 1 << 15, stream: bool = False,
+                           return_all: bool = False):
     """The DEEP stand-in's recipe (deep_like) drawn with a seeded torch
     generator on `device`, for workloads of tens of GB: the same mixture and
     parameters, other random numbers.  Rows 0..n-1 are cluster-partitioned as
     in cluster_partition (components sorted by a random projection of their
     means, assigned contiguously to segments of the given sizes) and written in
     partition order into one tensor; the segments are views of it (rows in
-    ascending order within a segment).  Returns (segments, queries)."""
+    ascending order within a segment).  With ``stream`` the rows stay in the
+    order they are drawn (arrival order) and segment k is the next sizes[k]
+    rows.  Returns (segments, queries), plus the whole tensor with
+    ``return_all``."""
     import torch
     g = torch.Generator(device=device)
     g.manual_seed(seed)
@@ -145,10 +149,13 @@ def deep_like_gpu_segments(n: int, nq: int, seed: int, sizes, part_seed: int, de
     sizes_t = torch.as_tensor(np.asarray(sizes, dtype=np.int64), device=device)
     bounds = torch.cat([torch.zeros(1, dtype=torch.int64, device=device), torch.cumsum(sizes_t, 0)])
     # destination of every row: its segment's start + its rank among that segment's rows
-    dest = torch.empty(n, dtype=torch.int64, device=device)
-    for k in range(len(sizes)):
-        rows = torch.sort(order[bounds[k]:bounds[k + 1]]).values
-        dest[rows] = bounds[k] + torch.arange(rows.numel(), device=device)
+    if stream:
+        dest = torch.arange(n, dtype=torch.int64, device=device)
+    else:
+        dest = torch.empty(n, dtype=torch.int64, device=device)
+        for k in range(len(sizes)):
+            rows = torch.sort(order[bounds[k]:bounds[k + 1]]).values
+            dest[rows] = bounds[k] + torch.arange(rows.numel(), device=device)
     del order
     allx = torch.empty((n, d), **f32)
     Q = torch.empty((nq, d), **f32)
@@ -166,6 +173,8 @@ def deep_like_gpu_segments(n: int, nq: int, seed: int, sizes, part_seed: int, de
             lo = max(s, n)
             Q[lo - n:e - n] = x[lo - s:]
     segs = [allx[int(bounds[k]):int(bounds[k + 1])] for k in range(len(sizes))]
+    if return_all:
+        return segs, Q, allx
     return segs, Q
 
 
