@@ -10,11 +10,13 @@ independent queries).  This module compiles it with gcc and wraps it with
 numpy arrays.  See that file's header for the paper passages each function
 follows.
 
-Parity status: beam search, prune, reverse-kNN inversion, pivot selection,
-IDPS cost, MOS and brute-force kNN are pinned by tests against brute force,
-exhaustive restatements, closed forms and invariants.  The end-to-end merge is
-pinned only by its parts, its invariants and the recall tolerance
-("parity unpinned" by the paper for the merge as a whole).
+Parity status: beam search, prune, reverse edges, neighbour expansion,
+reverse-kNN inversion, pivot selection, IDPS cost, MOS, recall@k and
+brute-force kNN are pinned by tests against hand-worked examples
+(tests/golden), brute force, exhaustive restatements, closed forms and
+invariants.  The end-to-end merge is pinned only by its parts, its invariants
+and the recall tolerance ("parity unpinned" by the paper for the merge as a
+whole).
 """
 from __future__ import annotations
 

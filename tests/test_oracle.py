@@ -487,3 +487,99 @@ def test_oracle_deterministic_across_thread_counts():
     a, _ = oracle.rnsm_merge(segs, graphs, entries, [(1, 0)], 8, 16, 1.2, threads=1)
     b, _ = oracle.rnsm_merge(segs, graphs, entries, [(1, 0)], 8, 16, 1.2, threads=4)
     np.testing.assert_array_equal(a, b)
+
+
+# ------------------------------------------- hand-worked pins (tests/golden)
+
+def _read_blocks(name):
+    """Lines of a golden file grouped into blocks ending with 'end'."""
+    blocks, cur = [], []
+    for parts in _lines(name):
+        if parts[0] == "end":
+            blocks.append(cur)
+            cur = []
+        else:
+            cur.append(parts)
+    if cur:
+        blocks.append(cur)
+    return blocks
+
+
+def test_mos_golden_trace():
+    # Algorithm 3, traced by hand: exact edge list (insertion order) and the
+    # degree-bound flags, including the cheapest vertex beyond Delta hops, a
+    # relay on either saturated end, the no-relay and both-saturated fallbacks
+    # and the tie rules.
+    blocks = _read_blocks("mos_trace.txt")
+    assert len(blocks) == 3
+    for blk in blocks:
+        C = np.array([[float(x) for x in p[1].split(",")] for p in blk if p[0] == "C"])
+        (rl,) = [p for p in blk if p[0] == "R"]
+        Rm, Delta = int(rl[1]), int(rl[3])
+        (el,) = [p for p in blk if p[0] == "E"]
+        want = [tuple(int(t) for t in e.split(",")) for e in el[1:]]
+        edges, flags = oracle.mos(C, Rm, Delta)
+        assert edges == [(a, b) for a, b, _ in want]
+        assert list(flags.astype(int)) == [f for _, _, f in want]
+        assert _diameter(C.shape[0], edges) <= Delta
+
+
+def test_reverse_edges_golden_line():
+    rows = _lines("reverse_edges_line.txt")
+    X = np.array([[float(x)] for x in rows[0][1].split(",")], np.float32)
+    (pl,) = [p for p in rows if p[0] == "P"]
+    R, alpha = int(pl[1]), float(pl[2])
+    lists = np.full((len(X), R), -1, np.int32)
+    for p in rows:
+        if p[0] == "L":
+            lists[int(p[1])] = [int(t) for t in p[2].split(",")]
+    eu = [int(p[1]) for p in rows if p[0] == "E"]
+    ev = [int(p[2]) for p in rows if p[0] == "E"]
+    want = lists.copy()
+    for p in rows:
+        if p[0] == "W":
+            want[int(p[1])] = [int(t) for t in p[2].split(",")]
+    got = oracle.reverse_edges(X, lists, eu, ev, alpha)
+    np.testing.assert_array_equal(got, want)
+    # The edge order does not matter (the pools are sets).
+    perm = np.random.default_rng(3).permutation(len(eu))
+    got2 = oracle.reverse_edges(X, lists, np.array(eu)[perm], np.array(ev)[perm], alpha)
+    np.testing.assert_array_equal(got2, want)
+
+
+def test_expand_golden_duplicates_and_evicted_seed():
+    X = np.array([[5.0], [5.0], [5.0], [9.0], [0.0]], np.float32)
+    n = len(X)
+    adj = np.array([[j for j in range(n) if j != i] for i in range(n)], np.int32)
+    for kp, rows in _lines("expand_duplicates.txt"):
+        want = np.array([[int(t) for t in r.split(",")] for r in rows.split(";")], np.int32)
+        got, _, _, _ = oracle.expand(X, adj, int(kp))
+        np.testing.assert_array_equal(got, want)
+
+
+@pytest.mark.parametrize("metric", [oracle.L2, oracle.IP])
+@pytest.mark.parametrize("k_plus", [1, 4, 15])
+def test_expand_complete_graph_is_bruteforce_without_self(metric, k_plus):
+    # On a complete graph the search seeded at v evaluates every vertex, so
+    # N+(v) is exactly the k+ nearest other vertices (no distance ties here).
+    n, d = 50, 6
+    X = gen.deep_like(n, seed=90 + k_plus, d=d)
+    adj = np.array([[j for j in range(n) if j != i] for i in range(n)], np.int32)
+    got, ndc, _, _ = oracle.expand(X, adj, k_plus, metric)
+    for v in range(n):
+        dist = _np_dist(X, X[v], metric)
+        dist[v] = np.inf
+        ref = np.lexsort((np.arange(n), dist))[:k_plus]
+        np.testing.assert_array_equal(got[v], ref)
+    assert (ndc == n).all()
+
+
+def test_recall_golden_ties():
+    rows = _lines("recall_ties.txt")
+    X = np.array([[float(x)] for x in rows[0][1].split(",")], np.float32)
+    Q = np.array([[float(x)] for x in rows[1][1].split(",")], np.float32)
+    gt = np.array([[float(x) for x in p[1].split(",")] for p in rows if p[0] == "G"])
+    assert gt.shape == (2, 11)
+    for case, q0, q1, want in (p for p in rows if p[0] in "abcd"):
+        found = np.array([[int(t) for t in q0.split(",")], [int(t) for t in q1.split(",")]])
+        assert oracle.recall_at_k(found, X, gt, Q, k=10) == pytest.approx(float(want)), case
