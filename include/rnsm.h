@@ -122,7 +122,6 @@ typedef struct {
     int64_t ndc;           /* distance computations of all searches */
     int64_t expansions;    /* beam expansions of all searches */
     int64_t rechecks;      /* prune decisions re-decided in FP32 */
-    int64_t near_ties;     /* reserved */
     int64_t pivots;        /* naive searches */
     int64_t followers;     /* local-sliding searches */
     int64_t reverse_edges; /* cross edges kept on the source side */
@@ -293,11 +292,14 @@ RNSM_API rnsm_status rnsm_prune(const float *vecs, int64_t n, int32_t dim, const
  *   Arguments, layout and results as rnsm_prune (prec is always FP32).
  *   nv > RNSM_PRUNE_NOALLOC_MAX_OWNERS gives RNSM_EINVAL.
  * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture.  Every call on a device shares the one array
- * (each call clears its counters first): calls that overlap on the GPU, from
- * several host threads or streams, race and must be serialised by the
- * caller.
+ * (cudaGetSymbolAddress, with that device current) and keeps it for the
+ * process; make that first call before any stream capture.  A device reset
+ * (cudaDeviceReset) reloads the module, so calls after one are invalid.
+ * Like every entry point here, the call synchronises `stream` (it reads the
+ * validation and error words back to the host) and returns once its outputs
+ * are written.  Every call on a device shares the one array (each call
+ * clears its counters first): calls that overlap on the GPU, from several
+ * host threads or streams, race and must be serialised by the caller.
  */
 #define RNSM_PRUNE_NOALLOC_MAX_OWNERS 262144
 RNSM_API rnsm_status rnsm_prune_noalloc(const float *vecs, int64_t n, int32_t dim,
@@ -330,7 +332,7 @@ RNSM_API rnsm_status rnsm_reverse_edges(const float *vecs, int64_t n, int32_t di
  * candidates).
  *   vecs, n, dim       device vectors
  *   p                  R, L, alpha, metric used
- *   batch_max          round size cap (0 selects max(64, n / 64))
+ *   batch_max          round size cap (0 selects n / 64 clamped to [64, 1024])
  *   out_adj            device [n * R] local ids, -1 padded
  *   out_entry          host: the entry vertex
  */

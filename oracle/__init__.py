@@ -228,8 +228,9 @@ def build_graph(X, R, L, alpha, metric=L2, batch_max=None, threads=0):
 
 
 def default_batch_max(n: int) -> int:
-    """Round size cap of the batch-synchronous build: n/64, at least 64."""
-    return max(64, n // 64)
+    """Round size cap of the batch-synchronous build: n/64 clamped to
+    [64, 1024] (the library's default)."""
+    return min(1024, max(64, n // 64))
 
 
 def bruteforce_knn(X, Q, k, metric=L2, threads=0):

@@ -1355,7 +1355,6 @@ rnsm_status rnsm_merge(const rnsm_segment *segs, int32_t m, const rnsm_params *p
         }
         stats->launches = launches_so_far() - launches0;
         stats->rechecks = (int64_t)rc;
-        stats->near_ties = 0;
         stats->pivots = n_piv;
         stats->followers = n_fol;
         stats->reverse_edges = (int64_t)rev_total;

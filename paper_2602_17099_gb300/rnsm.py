@@ -51,8 +51,8 @@ class MosEdge(C.Structure):
 
 class Stats(C.Structure):
     _fields_ = [("wall_s", C.c_double), ("host_pivot_s", C.c_double), ("ndc", C.c_int64),
-                ("expansions", C.c_int64), ("rechecks", C.c_int64), ("near_ties", C.c_int64),
-                ("pivots", C.c_int64), ("followers", C.c_int64), ("reverse_edges", C.c_int64),
+                ("expansions", C.c_int64), ("rechecks", C.c_int64), ("pivots", C.c_int64),
+                ("followers", C.c_int64), ("reverse_edges", C.c_int64),
                 ("launches", C.c_int64), ("phase_ms", C.c_double * 8),
                 ("search_ndc", C.c_int64 * 3), ("search_exp", C.c_int64 * 3),
                 ("search_queries", C.c_int64 * 3), ("tile_error", C.c_double * 4)]
@@ -277,6 +277,11 @@ def prune_noalloc(vecs, owners, pool, R, alpha, metric=L2, keep_all_if_fit=False
     nv = owners.shape[0]
     if out is None:
         out = torch.empty((nv, R), dtype=torch.int32, device=vecs.device)
+    elif tuple(out.shape) != (nv, R) or out.device != vecs.device:
+        # the kernel writes nv * R ids: a smaller or foreign buffer would be
+        # written past its end or on the wrong device
+        raise ValueError(f"out must have shape ({nv}, {R}) on {vecs.device}, "
+                         f"got {tuple(out.shape)} on {out.device}")
     _check(lib().rnsm_prune_noalloc(_dev(vecs, torch.float32, "vecs"), vecs.shape[0],
                                     vecs.shape[1], _dev(owners, torch.int32, "owners"), nv,
                                     _dev(pool, torch.int32, "pool"), pool.shape[1], R, alpha,

@@ -76,3 +76,36 @@ def test_noalloc_prune_rejects_batches_over_its_limit(rn):
                                      C.c_void_p(out.data_ptr()), None)
     assert st == rn.EINVAL
     assert b"static scratch limit" in rn.lib().rnsm_last_error()
+
+
+def test_noalloc_prune_leaves_device_memory_unchanged(rn):
+    # The point of this entry point: no device allocation inside the call.
+    # Warm-up calls load the kernels first (lazy module loading may map code
+    # memory); then the library workspace is released and the free device
+    # memory is read around calls that reach the general kernel (pools of
+    # 96) and the small-pool kernel (pools of 40).
+    X1, o1, p1 = _case(8, 6000, 128, 4000, 96)
+    X2, o2, p2 = _case(9, 3000, 32, 1500, 40)
+    out1 = torch.empty((o1.shape[0], 32), dtype=torch.int32, device="cuda")
+    out2 = torch.empty((o2.shape[0], 16), dtype=torch.int32, device="cuda")
+    for _ in range(2):
+        rn.prune_noalloc(X1, o1, p1, 32, 1.2, out=out1)
+        rn.prune_noalloc(X2, o2, p2, 16, 1.2, out=out2)
+    rn.release_workspace()
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    rn.prune_noalloc(X1, o1, p1, 32, 1.2, out=out1)
+    rn.prune_noalloc(X2, o2, p2, 16, 1.2, out=out2)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert torch.equal(out1, rn.prune(X1, o1, p1, 32, 1.2))
+
+
+def test_noalloc_prune_rejects_a_wrong_output_buffer(rn):
+    X, o, p = _case(10, 1000, 32, 10, 8)
+    with pytest.raises(ValueError):
+        rn.prune_noalloc(X, o, p, 16, 1.2, out=torch.empty((10, 15), dtype=torch.int32,
+                                                            device="cuda"))
+    with pytest.raises(ValueError):
+        rn.prune_noalloc(X, o, p, 16, 1.2, out=torch.empty((10, 16), dtype=torch.int32))
