@@ -806,13 +806,18 @@ typedef struct {
  * out_adj [N * R] global ids, initialised from the input graphs.
  * stats (nullable) [8]: ndc_expand, ndc_search, nexp_expand, nexp_search,
  * n_pivots_total, n_followers_total, n_dependent_pivots, reverse_edges.
+ * cm != 0: the Cross-query Merge comparator of Section 3.1 instead (the
+ * paper's CM baseline of Section 6: one-way naive search of every source
+ * vertex in the target, no expansion, pivots or sliding): S1-S3 are skipped,
+ * every source vertex is a pivot and S4 runs for all of them; S6 and S7 as
+ * for RNSM.
  */
 int32_t orc_rnsm_merge(const float *X, int64_t d, const int64_t *seg_off, int32_t m,
                        const int32_t *adj, int32_t r_in, const int32_t *entries, int32_t metric,
                        int32_t R, int32_t L, float alpha, int32_t k_rev, int32_t k_plus,
                        int32_t ef_slide, int32_t c_cross, const int32_t *plan_src,
                        const int32_t *plan_dst, int32_t n_plan, int32_t *out_adj, int64_t *stats,
-                       int32_t nthreads) {
+                       int32_t nthreads, int32_t cm) {
     if (m < 1 || R < 1 || L < 1 || r_in < 0 || r_in > R || k_rev < 1 || k_plus < k_rev ||
         ef_slide < 1 || ef_slide > L || c_cross < 1 || c_cross > ef_slide)
         return ORC_EINVAL;
@@ -868,16 +873,26 @@ int32_t orc_rnsm_merge(const float *X, int64_t d, const int64_t *seg_off, int32_
                 rc = ORC_ENOMEM;
                 goto done;
             }
-            rc = orc_expand(Xs, ns, d, Gs, r_in, metric, k_plus, c->nplus, ndcb, nexb, NULL,
-                            nthreads);
-            if (rc) goto done;
-            for (int64_t i = 0; i < ns; ++i) { st[0] += ndcb[i]; st[2] += nexb[i]; }
-            rc = orc_reverse_knn(c->nplus, ns, k_plus, k_rev, c->offs, c->rk);
-            if (rc) goto done;
-            int64_t dep = 0;
-            rc = orc_select_pivots(ns, c->offs, c->rk, c->pivot_of, c->pivots, &c->n_pivots, &dep);
-            if (rc) goto done;
-            st[6] += dep;
+            if (cm) {
+                /* CM: every vertex is a pivot, in id order */
+                for (int64_t v = 0; v < ns; ++v) {
+                    c->pivots[v] = (int32_t)v;
+                    c->pivot_of[v] = -1;
+                }
+                c->n_pivots = ns;
+            } else {
+                rc = orc_expand(Xs, ns, d, Gs, r_in, metric, k_plus, c->nplus, ndcb, nexb, NULL,
+                                nthreads);
+                if (rc) goto done;
+                for (int64_t i = 0; i < ns; ++i) { st[0] += ndcb[i]; st[2] += nexb[i]; }
+                rc = orc_reverse_knn(c->nplus, ns, k_plus, k_rev, c->offs, c->rk);
+                if (rc) goto done;
+                int64_t dep = 0;
+                rc = orc_select_pivots(ns, c->offs, c->rk, c->pivot_of, c->pivots, &c->n_pivots,
+                                       &dep);
+                if (rc) goto done;
+                st[6] += dep;
+            }
             c->computed = 1;
         }
         st[4] += c->n_pivots;

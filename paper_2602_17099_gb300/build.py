@@ -57,7 +57,10 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
         obj = os.path.join(OUT_DIR, os.path.basename(src) + ".o")
         cmd = [nvcc, *ARCH, *NVCC_FLAGS, *inc, *extra, "-c", src, "-o", obj]
         if src.endswith(".cpp"):
-            cmd = [nvcc, *NVCC_FLAGS, *inc, *extra, "-x", "c++", "-c", src, "-o", obj]
+            # host planners: no FMA contraction, so FP64 costs (and the plan order
+            # they decide) are the same on x86_64 and aarch64
+            cmd = [nvcc, *NVCC_FLAGS, "-Xcompiler", "-ffp-contract=off", *inc, *extra, "-x", "c++",
+                   "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"compile failed: {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")

@@ -1,0 +1,128 @@
+"""Precision modes, the multi-segment and embedding shapes and the CM
+comparator, each compared with the FP64 oracle's merge (not with the GPU's
+own FP32 path).
+
+* BF16 and FP8 prune tiles re-decide in FP32 every test their error bound
+  leaves open, so their merged graph must equal the GPU FP32 graph; that graph
+  is then held to the oracle: identical rows outside near ties, recall@10 of
+  the merged graphs within 0.005 at several search efforts, and the sampled
+  tile error inside its bound.
+* Shapes: deep-like d = 96 L2 over a MOS plan of five cluster-partitioned
+  segments of uneven size (the 10-segment DEEP-like workload at small scale);
+  embedding-like d = 768 inner product, R = 64, L = 128 over four random
+  segments (the embedding workload at small scale); real-valued rows far from
+  the origin (a common offset of 100), where a Gram tile that did not centre
+  its rows would cancel.
+* The Cross-query Merge comparator (Section 3.1) on integer data: bit-exact."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from workloads import generators as gen
+
+pytestmark = pytest.mark.gpu
+RECALL_TOL = 0.005
+
+
+@pytest.fixture(scope="module")
+def rn():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2602_17099_gb300 import build as b
+    b.build()
+    from paper_2602_17099_gb300 import rnsm
+    return rnsm
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    return t.cpu().numpy()
+
+
+def _recalls(X, G, Q, entry, gd, metric, efs):
+    seeds = np.full((len(Q), 1), entry, np.int32)
+    return [oracle.recall_at_k(oracle.beam_search(X, G, Q, seeds, ef, 10, metric)[0], X, gd, Q,
+                               metric=metric) for ef in efs]
+
+
+def _check_modes_against_oracle(rn, segs, Q, plan, R, L, metric, min_same=0.9,
+                                efs=(10, 16, 32, 64)):
+    gs = [oracle.build_graph(s, R, L, 1.2, metric=metric) for s in segs]
+    graphs, entries = [g for g, _ in gs], [e for _, e in gs]
+    want, _ = oracle.rnsm_merge(segs, graphs, entries, [(a, b) for a, b, *_ in plan], R, L, 1.2,
+                                metric=metric)
+    tsegs = [(dev(s), dev(g), e) for s, g, e in zip(segs, graphs, entries)]
+    fp32, s32 = rn.merge(tsegs, rn.params(R, L, 1.2, metric=metric), plan)
+    fp32 = host(fp32)
+    assert (fp32 == want).all(axis=1).mean() > min_same
+    X = np.concatenate(segs)
+    _, gd = oracle.bruteforce_knn(X, Q, 10, metric)
+    big = int(np.argmax([len(s) for s in segs]))
+    entry = int(np.concatenate([[0], np.cumsum([len(s) for s in segs])])[big]) + entries[big]
+    r_want = _recalls(X, want, Q, entry, gd, metric, efs)
+    r_got = _recalls(X, fp32, Q, entry, gd, metric, efs)
+    for ef, a, b in zip(efs, r_want, r_got):
+        assert abs(a - b) <= RECALL_TOL, (ef, a, b)
+    assert min(r_want) < 1.0          # the tolerance is exercised below recall 1
+    for prec in (rn.BF16, rn.FP8):
+        got, st = rn.merge(tsegs, rn.params(R, L, 1.2, metric=metric, prec=prec), plan)
+        np.testing.assert_array_equal(host(got), fp32)
+        assert st["tile_error"][3] > 0 and st["tile_error"][2] <= 1.0
+        assert st["rechecks"] > 0      # real-valued rows: some tests are left open
+    return r_want
+
+
+def test_modes_multi_segment_deep_like_against_oracle(rn):
+    # five uneven cluster-partitioned DEEP-like segments, MOS plan from sizes
+    # and centroids, d = 96, L2, R = 32, L = 64
+    sizes = [2600, 1500, 3400, 1900, 2300]
+    total = sum(sizes)
+    X, comp, means = gen.deep_like(total + 1000, 120, return_components=True)
+    parts = gen.cluster_partition(comp[:total], means, sizes, seed=121)
+    segs = [X[p].copy() for p in parts]
+    Q = X[total:].copy()
+    cen = np.stack([s.astype(np.float64).mean(0) for s in segs]).astype(np.float32)
+    plan = oracle.mos_plan(sizes, cen)
+    assert plan == rn.mos_plan(sizes, cen) and len(plan) >= 4
+    _check_modes_against_oracle(rn, segs, Q, plan, 32, 64, oracle.L2)
+
+
+def test_modes_embedding_shape_against_oracle(rn):
+    # four random segments of embedding-like rows, d = 768, inner product,
+    # R = 64, L = 128 (source pools of 128 candidates: the general tile)
+    X = gen.embed_like(4 * 1100 + 1000, 122, d=768, n_comp=60)
+    parts = gen.random_partition(4 * 1100, 4, 123)
+    segs = [X[p].copy() for p in parts]
+    Q = X[4 * 1100:].copy()
+    plan = oracle.mos_plan([len(s) for s in segs])
+    _check_modes_against_oracle(rn, segs, Q, plan, 64, 128, oracle.IP, min_same=0.85,
+                                efs=(10, 16, 32))
+
+
+def test_modes_offset_rows_against_oracle(rn):
+    # real-valued rows around a common offset of 100: components of about
+    # 100 +- 0.1, so squared norms are about 1e6 times the distances
+    segs = [gen.deep_like(3000, 124, d=96) + np.float32(100.0),
+            gen.deep_like(2200, 125, d=96) + np.float32(100.0)]
+    Q = gen.deep_like(1000, 126, d=96) + np.float32(100.0)
+    _check_modes_against_oracle(rn, segs, Q, [(1, 0, 0.0)], 32, 64, oracle.L2)
+
+
+@pytest.mark.parametrize("plan", [[(1, 0)], [(2, 0), (1, 0), (2, 1)]])
+def test_cm_comparator_exact_on_integer_data(rn, plan):
+    sizes = [1500, 900, 700]
+    segs = [gen.sift_like(n, 130 + i, d=64) for i, n in enumerate(sizes)]
+    gs = [oracle.build_graph(s, 16, 32, 1.2) for s in segs]
+    graphs, entries = [g for g, _ in gs], [e for _, e in gs]
+    want, wst = oracle.rnsm_merge(segs, graphs, entries, plan, 16, 32, 1.2, cm=True)
+    tsegs = [(dev(s), dev(g), e) for s, g, e in zip(segs, graphs, entries)]
+    for prec in (rn.FP32, rn.BF16):
+        got, gst = rn.merge(tsegs, rn.params(16, 32, 1.2, prec=prec, flags=rn.FLAG_CM),
+                            [(a, b, 0.0) for a, b in plan])
+        np.testing.assert_array_equal(host(got), want)
+        assert gst["pivots"] == wst["pivots"] and gst["followers"] == 0
+        assert gst["reverse_edges"] == wst["reverse_edges"]

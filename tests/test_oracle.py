@@ -583,3 +583,52 @@ def test_recall_golden_ties():
     for case, q0, q1, want in (p for p in rows if p[0] in "abcd"):
         found = np.array([[int(t) for t in q0.split(",")], [int(t) for t in q1.split(",")]])
         assert oracle.recall_at_k(found, X, gt, Q, k=10) == pytest.approx(float(want)), case
+
+
+def _cm_by_parts(segs, graphs, entries, plan, R, L, alpha, c_cross):
+    """Cross-query Merge (Section 3.1), composed from the pinned parts: for
+    each plan edge s -> t in order, every source vertex runs a naive beam
+    search of the frozen target graph from its entry (ef = L); its pool is its
+    current list and the first c_cross results; the pool is pruned; kept
+    cross edges add reverse edges into t."""
+    X = np.concatenate(segs)
+    off = np.concatenate([[0], np.cumsum([len(s) for s in segs])])
+    lists = np.full((len(X), R), -1, np.int32)
+    for s, g in enumerate(graphs):
+        r = g.shape[1]
+        lists[off[s]:off[s + 1], :r] = np.where(g >= 0, g + off[s], -1)
+    for s, t in plan:
+        Q = segs[s]
+        seeds = np.full((len(Q), 1), entries[t], np.int32)
+        res, _, _, _, _ = oracle.beam_search(segs[t], graphs[t], Q, seeds, L, L)
+        cross = np.where(res[:, :c_cross] >= 0, res[:, :c_cross] + off[t], -1)
+        owners = np.arange(off[s], off[s + 1], dtype=np.int64)
+        pool = np.concatenate([lists[off[s]:off[s + 1]], cross], axis=1).astype(np.int32)
+        new, _ = oracle.prune(X, owners, pool, R, alpha)
+        lists[off[s]:off[s + 1]] = new
+        eu, ev = [], []
+        for i, v in enumerate(owners):
+            for u in new[i]:
+                if off[t] <= u < off[t + 1]:
+                    eu.append(u)
+                    ev.append(v)
+        lists = oracle.reverse_edges(X, lists, np.array(eu, np.int32), np.array(ev, np.int32),
+                                     alpha)
+    return lists
+
+
+def test_cm_merge_equals_its_pinned_parts():
+    segs = [gen.gaussian(500, 8, 110), gen.gaussian(300, 8, 111), gen.gaussian(200, 8, 112)]
+    gs = [oracle.build_graph(s, 8, 16, 1.2) for s in segs]
+    graphs, entries = [g for g, _ in gs], [e for _, e in gs]
+    for plan in ([(1, 0)], [(2, 0), (1, 0), (2, 1)]):
+        got, st = oracle.rnsm_merge(segs, graphs, entries, plan, 8, 16, 1.2, cm=True)
+        want = _cm_by_parts(segs, graphs, entries, plan, 8, 16, 1.2, c_cross=8)
+        np.testing.assert_array_equal(got, want)
+        assert st["followers"] == 0 and st["ndc_expand"] == 0
+        assert st["pivots"] == sum(len(segs[s]) for s, _ in plan)
+    # RNSM's followers slide from their pivot's results instead: a different graph
+    rn_out, rst = oracle.rnsm_merge(segs, graphs, entries, [(1, 0)], 8, 16, 1.2)
+    assert rst["followers"] > 0
+    assert not np.array_equal(rn_out, oracle.rnsm_merge(segs, graphs, entries, [(1, 0)], 8, 16,
+                                                         1.2, cm=True)[0])
