@@ -44,6 +44,7 @@ PROFILE = os.path.join(ROOT, "profiles", "search_kernel_sift2x500k.txt")
 PRUNE_SRC = [os.path.join(ROOT, "paper_2602_17099_gb300", "csrc", f)
              for f in ("prune.cu", "common.cuh")]
 PRUNE_PROFILE = os.path.join(ROOT, "profiles", "prune_small_kernel_sift2x500k.txt")
+L2_PROFILE = os.path.join(ROOT, "profiles", "search_kernel_s5_sift2x200k.md")
 L2_METRIC, IP_METRIC = 0, 1
 
 
@@ -103,10 +104,10 @@ def _incremental(scale, nq):
 
 WORKLOADS = {
     "sift2x500k": Workload("sift2x500k", "sift-like 2x500k d128 L2 R32 L64 alpha1.2", 128, 32, 64,
-                           1.2, L2_METRIC, _sift, False, ("bf16", "fp8"), 0.1),
+                           1.2, L2_METRIC, _sift, False, ("bf16", "fp8"), 1.0),
     "deep10x2m": Workload("deep10x2m", "deep-like 10 segments (lognormal 50k-400k, 2M total, "
                           "cluster partition) d96 L2 R32 L64 alpha1.2, MOS plan", 96, 32, 64,
-                          1.2, L2_METRIC, _deep, True, ("bf16",), 0.02),
+                          1.2, L2_METRIC, _deep, True, ("bf16", "fp8"), 0.02),
     "embed4x250k": Workload("embed4x250k", "embedding-like 4x250k d768 IP R64 L128 alpha1.2, "
                             "MOS plan", 768, 64, 128, 1.2, IP_METRIC, _embed, True,
                             ("bf16", "fp8"), 0.01),
@@ -227,7 +228,10 @@ def oracle_sample(W, args, nq=10):
     ``W.oracle_scale`` of the full size (and nq queries of the same draw),
     graphs built by the oracle (untimed)."""
     import oracle
-    segs, Q = W.make(W.oracle_scale, nq)
+    if W.name == "sift2x500k" and args.n_per_seg:
+        segs, Q = _sift(1.0, nq, n_per_seg=args.n_per_seg)
+    else:
+        segs, Q = W.make(W.oracle_scale * args.scale, nq)
     segs = [to_host(s_) for s_ in segs]
     gs = [oracle.build_graph(s_, W.R, W.L, W.alpha, metric=W.metric) for s_ in segs]
     return oracle, segs, gs, to_host(Q)
@@ -250,10 +254,12 @@ def oracle_merge_once(W, oracle, segs, gs, keep=None):
     return time.perf_counter() - t0
 
 
-def recall_parity(W, oracle, segs, gs, Q, merged_oracle, rn, torch, ef=64):
+def recall_parity(W, oracle, segs, gs, Q, merged_oracle, rn, torch, efs=(10, 16, 64)):
     """Recall@10 of the oracle-merged and the GPU-merged graph of the same sample
     (same input graphs, same plan), both searched by the oracle's Algorithm 1
-    from the largest segment's entry, against the FP64 brute force."""
+    from the largest segment's entry, against the FP64 brute force, at several
+    search efforts (small ones keep recall below 1, where the 0.005 tolerance
+    means something)."""
     plan = sample_plan(W, oracle, segs)
     tsegs = [(torch.from_numpy(s_).cuda(), torch.from_numpy(g).cuda(), e) for s_, (g, e) in zip(segs, gs)]
     merged_gpu, _ = rn.merge(tsegs, rn.params(W.R, W.L, W.alpha, metric=W.metric),
@@ -265,24 +271,31 @@ def recall_parity(W, oracle, segs, gs, Q, merged_oracle, rn, torch, ef=64):
     entry = gs[big][1] + sum(sizes[:big])
     _, gd = oracle.bruteforce_knn(X, Q, 10, metric=W.metric)
     seeds = np.full((len(Q), 1), entry, np.int32)
-    out = {"queries": len(Q), "ef": ef,
-           "identical_rows": float((merged_gpu == merged_oracle).all(axis=1).mean())}
+    out = {"queries": len(Q), "ef": list(efs),
+           "identical_rows": float((merged_gpu == merged_oracle).all(axis=1).mean()),
+           "differing_rows": int((merged_gpu != merged_oracle).any(axis=1).sum())}
     for name, adj in (("oracle_merged", merged_oracle), ("gpu_merged", merged_gpu)):
-        ids = oracle.beam_search(X, adj, Q, seeds, ef, 10, metric=W.metric)[0]
-        out[name] = oracle.recall_at_k(ids, X, gd, Q, metric=W.metric)
+        out[name] = [oracle.recall_at_k(oracle.beam_search(X, adj, Q, seeds, ef, 10,
+                                                           metric=W.metric)[0],
+                                        X, gd, Q, metric=W.metric) for ef in efs]
+    out["max_abs_diff"] = max(abs(a - b) for a, b in zip(out["oracle_merged"], out["gpu_merged"]))
+    out["within_0.005"] = out["max_abs_diff"] <= 0.005
     return out
 
 
 def sample_desc(W, segs):
-    return (f"the same recipe at {W.oracle_scale:g} of full size: {len(segs)} segments, "
-            f"{sum(len(s_) for s_ in segs)} rows, FP64 C oracle with OpenMP")
+    what = ("the workload itself" if W.oracle_scale == 1.0 else
+            f"the same recipe at {W.oracle_scale:g} of the workload's size")
+    return (f"{what}: {len(segs)} segments, {sum(len(s_) for s_ in segs)} rows, input graphs "
+            f"built by the oracle (untimed), FP64 C oracle with OpenMP")
 
 
 def cpu_baseline(W, args, min_s=10.0, max_runs=40, rn=None, torch=None):
-    """The oracle's merge on the bounded sample, repeated until about min_s of CPU
-    time has been measured (the sample itself can take well under a second).
-    With the library at hand, also the recall parity of the two merged graphs."""
-    oracle, segs, gs, Q = oracle_sample(W, args, nq=200)
+    """The oracle's merge on the bounded sample (the SIFT-like default: the full
+    2 x 500k workload), repeated until about min_s of CPU time has been
+    measured.  With the library at hand, also the recall parity of the two
+    merged graphs on 1,000 queries."""
+    oracle, segs, gs, Q = oracle_sample(W, args, nq=1000)
     n = sum(len(s_) for s_ in segs)
     total, runs, keep = 0.0, 0, {}
     while runs < max_runs and (runs == 0 or total < min_s):
@@ -359,26 +372,60 @@ def prune_profile_traffic():
                            "dram bytes per S6 launch")
 
 
-def recall_at_10(rn, torch, W, Xd, adj, entry, Q, ef=64, chunk_rows=1 << 22, qb=64):
+def search_profile_l2():
+    """L2 throughput of the search kernel (percent of its peak) and its L2 hit
+    rate, from the committed small-case ncu capture of the current sources."""
+    out = {}
+    for key in ("l2 throughput pct (S5)", "l2 hit rate pct (S5)"):
+        v = profile_traffic(L2_PROFILE, SEARCH_SRC, "search sources sha256[:16]", key)
+        if v is not None:
+            out[key.replace(" (S5)", "").replace(" ", "_")] = v
+    if out:
+        out["source"] = os.path.relpath(L2_PROFILE, ROOT)
+    return out or None
+
+
+def recall_at_10(rn, torch, W, Xd, adj, entry, Q, ef=64, chunk_rows=1 << 22, qb=64, gt=None):
     """Tie-tolerant Recall@10 of the merged graph (evaluation only): a returned
     id counts if its FP64 distance is within the true 10th-NN distance.  The
     true neighbours come from a chunked FP32 scan (top 32 per query) re-ranked
-    in FP64.  entry: one global id, or a list (every query seeded with all)."""
+    in FP64 (``gt``: the 10th-NN distances of an earlier call, reused).
+    entry: one global id, or a list (every query seeded with all).  ``ef`` may
+    be a list: the recall at each."""
     Qd = Q if torch.is_tensor(Q) else torch.from_numpy(Q)
     Qd = Qd.cuda()
     nq = Qd.shape[0]
     ent = torch.tensor(entry if isinstance(entry, (list, tuple)) else [entry], dtype=torch.int32,
                        device="cuda")
     seeds = ent[None, :].expand(nq, ent.numel()).contiguous()
-    ids, _, _ = rn.search(Xd, adj, Qd, seeds, ef, 10, metric=W.metric)
 
     def native(rows64, q64):
         if W.metric == L2_METRIC:
             return ((rows64 - q64[:, None, :]) ** 2).sum(-1)
         return 1.0 - (rows64 * q64[:, None, :]).sum(-1)
 
-    hit = 0
-    for b in range(0, nq, qb):
+    d10 = gt if gt is not None else true_d10(torch, W, Xd, Qd, native, chunk_rows, qb)
+    efs = ef if isinstance(ef, (list, tuple)) else [ef]
+    res = []
+    for e in efs:
+        ids, _, _ = rn.search(Xd, adj, Qd, seeds, e, 10, metric=W.metric)
+        hit = 0
+        for b in range(0, nq, qb):
+            q64 = Qd[b:b + qb].double()
+            got = ids[b:b + qb]
+            ex = native(Xd[got.clamp(min=0).long()].double(), q64)
+            dk = d10[b:b + qb]
+            tol = 1e-9 * dk.abs()[:, None] + 1e-12
+            hit += ((ex <= dk[:, None] + tol) & (got >= 0)).sum().item()
+        res.append(hit / (10 * nq))
+    return res if isinstance(ef, (list, tuple)) else res[0]
+
+
+def true_d10(torch, W, Xd, Qd, native, chunk_rows=1 << 22, qb=64):
+    """FP64 10th-NN distance of every query: a chunked FP32 scan keeps the best 32
+    candidates of each query, re-ranked in FP64."""
+    out = []
+    for b in range(0, Qd.shape[0], qb):
         q = Qd[b:b + qb]
         best_d = best_i = None
         for c0 in range(0, Xd.shape[0], chunk_rows):
@@ -393,25 +440,23 @@ def recall_at_10(rn, torch, W, Xd, adj, entry, Q, ef=64, chunk_rows=1 << 22, qb=
                 dv, iv = torch.cat([best_d, dv], 1), torch.cat([best_i, iv], 1)
             sel = torch.topk(dv, min(32, dv.shape[1]), largest=False).indices
             best_d, best_i = torch.gather(dv, 1, sel), torch.gather(iv, 1, sel)
-        q64 = q.double()
-        d10 = torch.sort(native(Xd[best_i].double(), q64), dim=1).values[:, 9]
-        got = ids[b:b + qb]
-        ex = native(Xd[got.clamp(min=0).long()].double(), q64)
-        tol = 1e-9 * d10.abs()[:, None] + 1e-12
-        hit += ((ex <= d10[:, None] + tol) & (got >= 0)).sum().item()
-    return hit / (10 * nq)
+        out.append(torch.sort(native(Xd[best_i].double(), q.double()), dim=1).values[:, 9])
+    return torch.cat(out)
 
 
 def concat_rows(torch, vd):
     """The segments as one [N, d] table: a view when they already sit back to
     back in one allocation (device-drawn workloads), else a copy."""
     d = vd[0].shape[1]
+    st = vd[0].untyped_storage()
     p, off = vd[0].data_ptr(), 0
     for v in vd:
-        if v.data_ptr() != p + off * d * 4 or not v.is_contiguous():
-            return torch.cat(vd)
+        if (v.untyped_storage().data_ptr() != st.data_ptr() or v.data_ptr() != p + off * d * 4
+                or not v.is_contiguous()):
+            return torch.cat(vd)   # separate allocations (even when adjacent)
         off += v.shape[0]
-    return vd[0].as_strided((off, d), (d, 1))
+    return torch.empty(0, dtype=vd[0].dtype, device=vd[0].device).set_(
+        st, vd[0].storage_offset(), (off, d), (d, 1))
 
 
 def e2e_room(torch, in_bytes, out_bytes):
@@ -539,26 +584,36 @@ def run_ours(args, ws, rank, local):
                    "traffic": traffic,
                    "algorithmic_bytes_per_launch": s_bytes / n_search_launches,
                    "avg_launch_ms": s_ms / n_search_launches,
-                   "note": "algorithmic bytes; most are served from L2 (see traffic)"}
-    # roofline of the S6 source prune (FP32, CUDA cores): per owner the distances
-    # of all (c+1) c / 2 pairs of its pool rows and its own row over d dimensions,
-    # 3 FLOP per dimension for L2 (subtraction, fused multiply-add), 2 for IP;
-    # peak = SMs x 128 FP32 lanes x 2 FLOP x maximum SM clock
+                   "l2": search_profile_l2(),
+                   "note": "algorithmic bytes; most are served from L2 (see traffic and l2)"}
+    # roofline of the S6 source prune, in the unit of its per-owner gather: the
+    # owner row and its c = R + c_cross raw pool rows, d x 4 bytes each, per
+    # owner (every source vertex), against the measured HBM copy bandwidth
     pool = W.R + (W.L + 1) // 2
-    fl_per_owner = (pool + 1) * pool / 2 * W.dim * (3 if W.metric == L2_METRIC else 2)
-    p_flop = sum((st["pivots"] + st["followers"]) * fl_per_owner for st in stats)
+    b_per_owner = (pool + 1) * W.dim * 4
+    owners = sum(st["pivots"] + st["followers"] for st in stats)
     p_ms = sum(st["phase_ms"][6] for st in stats)
     n_p6 = len(stats) * (len(plan_used) if plan_used else 1)
+    p_ach = owners * b_per_owner / (p_ms / 1000.0) / 1e9
+    prune_roof = {"bound": "hbm",
+                  "kernel": ("prune_small_kernel" if pool <= 64 else "prune_kernel") + " (S6 launches)",
+                  "achieved": p_ach, "peak": peak, "unit": "GB/s", "frac": p_ach / peak,
+                  "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+                  "traffic": prune_profile_traffic() if full_default else None,
+                  "algorithmic_bytes_per_launch": owners * b_per_owner / n_p6,
+                  "algorithmic_bytes_per_owner": b_per_owner,
+                  "avg_launch_ms": p_ms / n_p6}
+    # the same launches as FP32 arithmetic: at most R x c occlusion tests per
+    # owner (the walk tests a candidate only against kept ones), 2 FLOP per
+    # dimension, against SMs x 128 FP32 lanes x 2 FLOP x the maximum SM clock
     sm_count = torch.cuda.get_device_properties(0).multi_processor_count
     alu_peak = sm_count * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
-    p_ach = p_flop / (p_ms / 1000.0) / 1e12
-    prune_roof = {"bound": "alu",
-                  "kernel": ("prune_small_kernel" if pool <= 64 else "prune_kernel") + " (S6 launches)",
-                  "achieved": p_ach, "peak": alu_peak, "unit": "TFLOP/s", "frac": p_ach / alu_peak,
+    f_ach = owners * W.R * pool * W.dim * 2 / (p_ms / 1000.0) / 1e12
+    prune_flop = {"bound": "alu", "kernel": prune_roof["kernel"], "achieved_at_most": f_ach,
+                  "peak": alu_peak, "unit": "TFLOP/s", "frac_at_most": f_ach / alu_peak,
                   "peak_source": "derived: %d SMs x 128 FP32 lanes x 2 FLOP x %.0f MHz" % (
                       sm_count, float(peaks.get("sm_max_mhz", 2070.0))),
-                  "traffic": prune_profile_traffic() if full_default else None,
-                  "algorithmic_flop_per_launch": p_flop / n_p6, "avg_launch_ms": p_ms / n_p6}
+                  "flop_per_owner_at_most": W.R * pool * W.dim * 2}
     # the dominant kernel family of the FP32 step by live time goes first
     s7_ms = sum(st["phase_ms"][7] for st in stats)
     if p_ms + s7_ms >= s_ms:
@@ -658,7 +713,7 @@ def run_ours(args, ws, rank, local):
         del pin_v, pin_g, pin_out, dv, dg
 
     progress(f"e2e: {e2e.get('value')}")
-    rec = None
+    rec = Xd = None
     if rank == 0 and args.recall_queries > 0:
         Xd = concat_rows(torch, vd)
         big = int(np.argmax(sizes))
@@ -674,6 +729,7 @@ def run_ours(args, ws, rank, local):
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         base = cpu_baseline(W, args, rn=rn, torch=torch)
 
+    line = None
     if rank == 0:
         vec_bytes = sum(v.numel() * 4 for v in vd)
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
@@ -695,12 +751,132 @@ def run_ours(args, ws, rank, local):
                            "ndc_per_step": stats[-1]["ndc"]},
                 "clocks": clocks, "e2e": e2e, "gpu_launches": int(launches),
                 "precision_modes": modes,
-                "roofline": roofline, "roofline_secondary": roofline_other, "cpu_baseline": base}
+                "roofline": roofline, "roofline_secondary": roofline_other,
+                "roofline_prune_flop": prune_flop, "cpu_baseline": base}
+    full_headline = W.name == "sift2x500k" and args.scale == 1.0 and not args.n_per_seg
+    extra = (rank == 0 and ws == 1 and not args.no_extra and W.name == "sift2x500k" and
+             (full_headline or args.extra_scale is not None))
+    if extra:
+        # the larger workloads, measured after the headline (its memory freed)
+        del vd, graphs, tsegs, out, ref_out, Xd
+        rn.release_workspace()
+        torch.cuda.empty_cache()
+        line["extra_workloads"] = run_extra(rn, torch, args.extra_scale or 1.0)
+    if rank == 0:
         print(json.dumps(line), flush=True)
     barrier(dist)
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+EXTRA = (("deep10x2m", 2, 1), ("embed4x250k", 2, 1), ("deep50x100m", 1, 1))
+CURVE_EFS = [16, 32, 64, 128, 256]
+
+
+def run_extra(rn, torch, scale=1.0, nq=1000):
+    """The multi-segment workloads at full size, a few steps each: FP32 and
+    low-precision ms/step, re-decided tests, graph identity, recall@10; for the
+    10-segment DEEP-like workload also the CM comparator and a rebuild by the
+    same builder (merge time and recall@10 curves)."""
+    res = {}
+    for name, steps, warm in EXTRA:
+        W = WORKLOADS[name]
+        try:
+            res[name] = measure_extra(W, rn, torch, steps, warm, nq, scale,
+                                      curves=name == "deep10x2m")
+        except Exception as e:   # noqa: BLE001 -- one workload's failure is reported, not fatal
+            res[name] = {"error": f"{type(e).__name__}: {e}"}
+        rn.release_workspace()
+        torch.cuda.empty_cache()
+        progress(f"extra workload {name} done")
+    return res
+
+
+def measure_extra(W, rn, torch, steps, warm, nq, scale=1.0, curves=False):
+    segs, Q = W.make(scale, nq)
+    vd = [s_ if torch.is_tensor(s_) else torch.from_numpy(s_).cuda() for s_ in segs]
+    del segs
+    sizes = [int(v.shape[0]) for v in vd]
+    N = sum(sizes)
+    cen = centroids_of(vd)
+    progress(f"{W.name}: {len(vd)} segments, {N} rows on the device")
+    t0 = time.perf_counter()
+    graphs = [rn.build_segment(v, W.R, W.L, W.alpha, metric=W.metric) for v in vd]
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    tsegs = [(v, g, e) for v, (g, e) in zip(vd, graphs)]
+    stream = torch.cuda.current_stream()
+
+    def timed(p, out):
+        for _ in range(warm):
+            rn.merge(tsegs, p, plan=rn.mos_plan(sizes, cen), out=out)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            _, st = rn.merge(tsegs, p, plan=rn.mos_plan(sizes, cen), out=out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps, st
+
+    out = torch.empty((N, W.R), dtype=torch.int32, device="cuda")
+    ms32, st32 = timed(rn.params(W.R, W.L, W.alpha, metric=W.metric), out)
+    r = {"workload": W.desc, "scale": scale, "segments": sizes,
+         "plan_edges": len(rn.mos_plan(sizes, cen)),
+         "steps": steps, "warmup": warm, "input_graph_build_s": round(build_s, 3),
+         "fp32": {"ms_per_step": ms32, "value": N / (ms32 / 1000.0), "unit": UNIT,
+                  "phase_ms": [round(x, 3) for x in st32["phase_ms"]]}}
+    oq = torch.empty_like(out)
+    for name in W.modes:
+        prec = {"bf16": rn.BF16, "fp8": rn.FP8}[name]
+        msq, stq = timed(rn.params(W.R, W.L, W.alpha, metric=W.metric, prec=prec), oq)
+        r[name] = {"ms_per_step": msq, "value": N / (msq / 1000.0), "unit": UNIT,
+                   "identical_to_fp32": bool(torch.equal(oq, out)),
+                   "rechecks_per_step": int(stq["rechecks"]),
+                   "tile_vs_fp32_max_share_of_bound": stq["tile_error"][2],
+                   "prune_ms": round(stq["phase_ms"][6] + stq["phase_ms"][7], 3)}
+    del oq
+    Xd = concat_rows(torch, vd)
+    Qd = (Q if torch.is_tensor(Q) else torch.from_numpy(Q)).cuda()
+    big = int(np.argmax(sizes))
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    entry = int(graphs[big][1] + offs[big])
+    efs = CURVE_EFS if curves else [64]
+    gt = None
+
+    def curve(adj, ent):
+        nonlocal gt
+        if gt is None:
+            def native(rows64, q64):
+                if W.metric == L2_METRIC:
+                    return ((rows64 - q64[:, None, :]) ** 2).sum(-1)
+                return 1.0 - (rows64 * q64[:, None, :]).sum(-1)
+            gt = true_d10(torch, W, Xd, Qd, native)
+        return dict(zip(map(str, efs), recall_at_10(rn, torch, W, Xd, adj, ent, Qd, ef=efs, gt=gt)))
+
+    r["recall_at_10"] = {"queries": nq, "rnsm": curve(out, entry)}
+    if curves:
+        # the CM comparator (every source vertex a naive search) on the same plan
+        oc = torch.empty_like(out)
+        msc, stc = timed(rn.params(W.R, W.L, W.alpha, metric=W.metric, flags=rn.FLAG_CM), oc)
+        r["cm"] = {"ms_per_step": msc, "value": N / (msc / 1000.0), "unit": UNIT,
+                   "naive_searches": int(stc["pivots"]), "rnsm_over_cm_speedup": msc / ms32}
+        r["recall_at_10"]["cm"] = curve(oc, entry)
+        del oc
+        # a rebuild of all rows by the same builder
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        gr, er = rn.build_segment(Xd, W.R, W.L, W.alpha, metric=W.metric)
+        torch.cuda.synchronize()
+        rb_s = time.perf_counter() - t0
+        r["rebuild"] = {"s": rb_s, "rnsm_over_rebuild_speedup": rb_s / (ms32 / 1000.0)}
+        r["recall_at_10"]["rebuild"] = curve(gr, int(er))
+        r["recall_at_10"]["rnsm_segment_entries"] = curve(
+            out, [int(graphs[k][1] + offs[k]) for k in range(len(sizes))])
+        del gr
+    del out, tsegs, graphs, vd, Xd
+    return r
 
 
 def run_incremental(args, ws, rank, local):
@@ -822,6 +998,11 @@ def main():
                     help="sift2x500k only: rows per segment (overrides --scale)")
     ap.add_argument("--recall-queries", type=int, default=1000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the multi-segment workloads the default run also measures")
+    ap.add_argument("--extra-scale", type=float, default=None,
+                    help="size factor of those workloads (default: full size, measured only "
+                         "after the full-size default workload)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -816,11 +816,14 @@ cudaError_t launch_small(const PruneArgs &a, cudaStream_t st);
 cudaError_t launch_prune(const PruneArgs &a, cudaStream_t st) {
     if (a.n_owners <= 0) return cudaSuccess;
     if (a.R > 64 || a.dim > 1024 || (a.dim & 3)) return cudaErrorInvalidValue;
-    // BF16 at small L2 dimensions: the pair tile; pools too large for it take the
-    // general tile with the FP32 rows split into two terms (no stored copies)
+    // BF16 / FP8 at small L2 dimensions: the pair tile; BF16 pools too large for it
+    // take the general tile with the FP32 rows split into two terms, FP8 ones the
+    // FP32 kernels (no stored copies either way)
     const bool pair_ok = a.prec != 0 && prune_pair_ok(a.dim, a.prec, a.metric);
     const bool pair = pair_ok && a.lenA + a.lenB <= prune_pair_max_pool();
-    const int terms = pair ? 0 : pair_ok ? 2 : a.prec != 0 ? prune_tc_terms(a.dim, a.prec) : 0;
+    const int terms = pair ? 0
+                      : pair_ok ? (a.prec == 1 ? 2 : 0)
+                      : a.prec != 0 ? prune_tc_terms(a.dim, a.prec) : 0;
     const bool tc = terms == 2 || (terms == 1 && a.qrows);
     const int cap = pair ? prune_pair_max_pool() : tc ? prune_tc_max_pool() : kSmallMax;
     const bool small_ok = a.ovf_list && a.ovf_count && a.work2 && a.lenA + a.lenB <= cap;

@@ -1,5 +1,6 @@
-// K4b: the BF16 tensor-core prune for small pools (L2, at most 64 raw
-// candidates, dimension a multiple of 16 up to 128), two owners per tile.
+// K4b: the BF16 / FP8 tensor-core prune for small pools (L2, at most 64 raw
+// candidates, dimension a multiple of 16 (BF16) or 32 (FP8) up to 128), two
+// owners per tile.
 //
 // The general tensor-core prune (prune_tc.cu) gives one CTA of eight warps to
 // one owner and spends most of its time in barrier-separated phases; for pools
@@ -38,18 +39,33 @@
 //     index is the number of kept slots before it, and the cap keeps the
 //     first R.  The other warp prefetches the next owner's rows into L2.
 //
+// FP8 (E4M3) tiles stage the same centred row in two E4M3 terms with a
+// per-row power-of-two scale sigma_r (the largest with sigma_r max|y| <= 448,
+// found in a first pass over the row that also runs the FP32 chain):
+// hi = e4m3(sigma_r y), lo = e4m3(sigma_r y - hi); the MMAs (kind::f8f6f4,
+// K = 32) accumulate sigma_s sigma_c (hi + lo)_s . (hi + lo)_c, and the tile
+// values are unscaled by 1 / (sigma_s sigma_c), exactly (powers of two).  Two
+// E4M3 terms carry 8 significant bits: integer differences of magnitude <= 256
+// are staged exactly (the same whole-table check as the BF16 hi-only case),
+// otherwise the staging error is at most about 2^-8 of the row.
+//
 // The result equals the FP32 prune's: the order is exact, and every
 // occlusion decision either follows from a proven bound or is taken in FP32.
 //
 // Bound (per pair s, c; x~ the staged row, x the centred FP32 row):
 //   staging   |x~ - (x_c - x_v)| <= kE |x~| element-wise, kE = 1.0002 (2^-16 + 2^-24)
 //             (2^-24 (1.0001) when every lo is zero);
+//             FP8: ||x~ - (x_c - x_v)|| <= kE ||x~||, kE = 1.01 (1.004 2^-8 + 2^-24 + c),
+//             c = sqrt(dim) 2^-10 / 224 covering E4M3 subnormals (half their
+//             spacing, 2^-10, against a scaled row of max |.| >= 224), or the
+//             hi-only constant when the whole table is integer with range <= 256;
 //   Gram      |G~_ij - x~_i . x~_j| <= e1 n_i n_j, e1 = 1.01 eps_c, eps_c =
 //             1.01 (n_instr + 1) 2^-22 (the per-MMA-instruction accumulation
 //             model of the general kernel; sampled tile statistics check it);
 //   FP32      |d_fp32 - d| <= gam d, gam = 1.01 (dim + 2) 2^-24;
 //   so |d~ - d_fp32| <= kappa (n_s + n_c)^2, kappa = 1.01 (e1 + 2 kE + kE^2 + gam (1 + kE)^2).
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 #include <float.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -79,6 +95,7 @@ struct PairSmem {
     float gd[2][kQC];                      // Gram diagonal
     float nn[2][kQC];                      // bound on the staged row's squared norm
     float2 pq[2][kQC];                     // column terms of the occlusion test
+    float isc[2][kQC];                     // FP8: 1 / sigma of each slot's staged row
     uint32_t occ[2][kQC][2];               // occluders of slot c, by slot
     uint32_t live[2][2];                   // valid slots (ids not repeated), per warp
     uint64_t bar;
@@ -122,11 +139,33 @@ __device__ __noinline__ int decide_open(float g, float gs, float ns2, float gc, 
     return (fmaf(alpha, d, -dvc) <= 0.f ? 1 : 0) | 2;
 }
 
-// kHiOnly: every component of every row is an integer and their range is at
-// most 256 (checked on the device before the launch), so y = x_c - x_v is exact
-// in FP32 and in BF16: the tile holds hi only (half the shared memory).
-template <bool kHiOnly>
+// Packs two floats into two E4M3 bytes (x in the low byte), rounding to
+// nearest, saturating at 448.
+__device__ __forceinline__ uint32_t e4m3x2(float x, float y) {
+    return (uint32_t)__nv_cvt_float2_to_fp8x2(make_float2(x, y), __NV_SATFINITE, __NV_E4M3);
+}
+__device__ __forceinline__ float2 e4m3x2_to_float2(uint32_t v) {
+    const __half2_raw h = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)v, __NV_E4M3);
+    return __half22float2(*reinterpret_cast<const __half2 *>(&h));
+}
+
+// Largest power of two sigma with sigma * m <= 448 (1 for m = 0).
+// (448 = 0.875 2^9; the exponent is capped so that sigma stays a normal float.)
+__device__ __forceinline__ float e4m3_scale(float m) {
+    if (!(m > 0.f)) return 1.f;
+    int E;
+    const float f = frexpf(m, &E);   // m = f 2^E, f in [0.5, 1)
+    return ldexpf(1.0f, min((f <= 0.875f ? 9 : 8) - E, 126));
+}
+
+// kKind 0: BF16 hi and lo terms; 1: BF16 hi only -- every component of every
+// row is an integer and their range is at most 256 (checked on the device
+// before the launch), so y = x_c - x_v is exact in FP32 and in BF16 (half the
+// shared memory); 2: two E4M3 terms with per-row power-of-two scales.
+template <int kKind>
 __global__ void __launch_bounds__(kQT) prune_pair_kernel(const PruneArgs a, int chunk) {
+    constexpr bool kHiOnly = kKind == 1;
+    constexpr bool kF8 = kKind == 2;
     extern __shared__ __align__(1024) unsigned char tile[];
     __shared__ PairSmem s;
     __shared__ int64_t sh_i;
@@ -136,9 +175,15 @@ __global__ void __launch_bounds__(kQT) prune_pair_kernel(const PruneArgs a, int 
     const int dim = a.dim, R = a.R;
     const float alpha = a.alpha;
     const int U = dim >> 3;                  // 16-byte units of a BF16 row
-    const uint32_t SBO = 16u * (uint32_t)dim;   // bytes between 8-row core-matrix bands
-    const uint32_t region = 128u * 2u * (uint32_t)dim;   // one term (hi or lo) of the tile
+    const uint32_t esz = kF8 ? 1u : 2u;      // bytes per staged element
+    const uint32_t SBO = 8u * esz * (uint32_t)dim;   // bytes between 8-row core-matrix bands
+    const uint32_t region = 128u * esz * (uint32_t)dim;   // one term (hi or lo) of the tile
     const float gam = 1.01f * (float)(dim + 2) * 5.9604645e-08f;
+    // FP8: the staging bound (the whole-table exact case reuses the hi-only constant)
+    const float kE8 = a.pair_hi_only
+                          ? 1.0001f * 5.9604645e-08f
+                          : 1.01f * (1.004f * 3.90625e-03f + 5.9604645e-08f +
+                                     sqrtf((float)dim) * 9.765625e-04f / 224.0f);
 
     if (tid == 0) {
         tc::mbar_init(&s.bar, 1);
@@ -237,11 +282,112 @@ __global__ void __launch_bounds__(kQT) prune_pair_kernel(const PruneArgs a, int 
             unsigned char *hrow = tile + (uint32_t)(r >> 3) * SBO + (uint32_t)(r & 7) * 16u;
             bool lo_any = false;
             float dxt = INFINITY;
+            float isc_t = 1.f;
             if (!valid_t) {
-                for (int u = 0; u < U; ++u) {
+                for (int u = 0; u < (kF8 ? U / 2 : U); ++u) {
                     *reinterpret_cast<uint4 *>(hrow + u * 128) = make_uint4(0u, 0u, 0u, 0u);
                     if (!kHiOnly)
                         *reinterpret_cast<uint4 *>(hrow + region + u * 128) = make_uint4(0u, 0u, 0u, 0u);
+                }
+            } else if (kF8 && a.pair_hi_only) {
+                // integer rows spanning <= 256: |v - x| <= 256 is staged exactly with
+                // sigma = 1, so one pass gives the FP32 prune distance (chains E and O
+                // over v - x, in order) and the two terms
+                f2_t acc = 0ull;
+                const float *v = s.vrow[o];
+                for (int u = 0; u < U / 2; ++u) {   // 16 dimensions per 16-byte unit
+                    float4 x4[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) x4[q] = ldg4(xrow + 16 * u + 4 * q);
+                    uint32_t hw[4], lw[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const float4 v4 = *reinterpret_cast<const float4 *>(v + 16 * u + 4 * q);
+                        const f2_t y01 = f2_sub(f2_of(v4.x, v4.y), f2_of(x4[q].x, x4[q].y));
+                        acc = f2_fma(y01, y01, acc);
+                        const f2_t y23 = f2_sub(f2_of(v4.z, v4.w), f2_of(x4[q].z, x4[q].w));
+                        acc = f2_fma(y23, y23, acc);
+                        float z0, z1, z2, z3;
+                        f2_split(y01, z0, z1);
+                        f2_split(y23, z2, z3);
+                        const uint32_t h01 = e4m3x2(z0, z1), h23 = e4m3x2(z2, z3);
+                        const float2 f01 = e4m3x2_to_float2(h01), f23 = e4m3x2_to_float2(h23);
+                        hw[q] = h01 | (h23 << 16);
+                        lw[q] = e4m3x2(z0 - f01.x, z1 - f01.y) | (e4m3x2(z2 - f23.x, z3 - f23.y) << 16);
+                    }
+                    if (whole) {
+                        hw[0] = hw[1] = hw[2] = hw[3] = 0u;
+                        lw[0] = lw[1] = lw[2] = lw[3] = 0u;
+                    }
+                    lo_any |= ((lw[0] | lw[1] | lw[2] | lw[3]) & 0x7f7f7f7fu) != 0u;
+                    *reinterpret_cast<uint4 *>(hrow + u * 128) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                    *reinterpret_cast<uint4 *>(hrow + region + u * 128) =
+                        make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                }
+                dxt = chain2_final(acc, 0);
+            } else if (kF8) {
+                // pass 1: the FP32 prune distance (chains E and O over v - x, in order)
+                // and max |v - x|; pass 2: the same v - x, scaled by sigma, in two terms
+                f2_t acc = 0ull;
+                float ymax = 0.f;
+                const float *v = s.vrow[o];
+                for (int u0 = 0; u0 < U; u0 += 4) {
+                    float4 xa[4][2];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        if (u0 + k < U) {
+                            xa[k][0] = ldg4(xrow + 8 * (u0 + k));
+                            xa[k][1] = ldg4(xrow + 8 * (u0 + k) + 4);
+                        }
+                    }
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const int u = u0 + k;
+                        if (u >= U) break;
+                        const float4 v0 = *reinterpret_cast<const float4 *>(v + 8 * u);
+                        const float4 v1 = *reinterpret_cast<const float4 *>(v + 8 * u + 4);
+                        const f2_t xs[4] = {f2_of(xa[k][0].x, xa[k][0].y), f2_of(xa[k][0].z, xa[k][0].w),
+                                            f2_of(xa[k][1].x, xa[k][1].y), f2_of(xa[k][1].z, xa[k][1].w)};
+                        const f2_t vs[4] = {f2_of(v0.x, v0.y), f2_of(v0.z, v0.w), f2_of(v1.x, v1.y),
+                                            f2_of(v1.z, v1.w)};
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const f2_t y = f2_sub(vs[e], xs[e]);
+                            acc = f2_fma(y, y, acc);
+                            float y0, y1;
+                            f2_split(y, y0, y1);
+                            ymax = fmaxf(ymax, fmaxf(fabsf(y0), fabsf(y1)));
+                        }
+                    }
+                }
+                dxt = chain2_final(acc, 0);
+                const float sg = e4m3_scale(ymax);
+                isc_t = 1.0f / sg;   // a power of two: exact
+                for (int u = 0; u < U / 2; ++u) {   // 16 dimensions per 16-byte unit
+                    uint32_t hw[4], lw[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const float4 x4 = ldg4(xrow + 16 * u + 4 * q);
+                        const float4 v4 = *reinterpret_cast<const float4 *>(v + 16 * u + 4 * q);
+                        // y exactly as in pass 1, scaled exactly (sg is a power of two)
+                        const float z0 = (v4.x - x4.x) * sg, z1 = (v4.y - x4.y) * sg;
+                        const float z2 = (v4.z - x4.z) * sg, z3 = (v4.w - x4.w) * sg;
+                        const uint32_t h01 = e4m3x2(z0, z1), h23 = e4m3x2(z2, z3);
+                        const float2 f01 = e4m3x2_to_float2(h01), f23 = e4m3x2_to_float2(h23);
+                        // z - hi is exact in FP32
+                        const uint32_t l01 = e4m3x2(z0 - f01.x, z1 - f01.y);
+                        const uint32_t l23 = e4m3x2(z2 - f23.x, z3 - f23.y);
+                        hw[q] = h01 | (h23 << 16);
+                        lw[q] = l01 | (l23 << 16);
+                    }
+                    if (whole) {   // no tests: the tile rows stay zero
+                        hw[0] = hw[1] = hw[2] = hw[3] = 0u;
+                        lw[0] = lw[1] = lw[2] = lw[3] = 0u;
+                    }
+                    lo_any |= ((lw[0] | lw[1] | lw[2] | lw[3]) & 0x7f7f7f7fu) != 0u;
+                    *reinterpret_cast<uint4 *>(hrow + u * 128) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                    *reinterpret_cast<uint4 *>(hrow + region + u * 128) =
+                        make_uint4(lw[0], lw[1], lw[2], lw[3]);
                 }
             } else {
                 // the FP32 prune distance, chains E (even dimensions) and O (odd) over
@@ -317,23 +463,36 @@ __global__ void __launch_bounds__(kQT) prune_pair_kernel(const PruneArgs a, int 
             s.key[o][t] = keyt;
             s.sd[o][t] = dxt;
             s.rp[o][t] = xrow;
+            if (kF8) s.isc[o][t] = isc_t;
             // ---- 3. the Gram tile -----------------------------------------------
-            const int n_instr = (four ? 4 : 1) * (dim >> 4);
+            const int n_instr = (four ? 4 : 1) * (dim >> (kF8 ? 5 : 4));
             const float eps_c = 1.01f * (float)(n_instr + 1) * 2.384185791e-07f;
             const float e1 = 1.01f * eps_c;
-            const float kE = four ? 1.0002f * (1.52587890625e-05f + 5.9604645e-08f) : 1.0001f * 5.9604645e-08f;
+            const float kE = kF8 ? kE8
+                                 : four ? 1.0002f * (1.52587890625e-05f + 5.9604645e-08f)
+                                        : 1.0001f * 5.9604645e-08f;
             const float kappa = 1.01f * (e1 + 2.0f * kE + kE * kE + gam * (1.0f + kE) * (1.0f + kE));
             const float cb = 2.0f * kappa + 1e-6f;
             if (tid == 0) {
-                const uint32_t idesc = tc::instr_desc(1u, 128, 128);
-                for (int k = 0; k < (dim >> 4); ++k) {
+                // one K-step = 32 bytes of each row: 16 BF16 or 32 E4M3 elements
+                const uint32_t idesc = tc::instr_desc(kF8 ? 0u : 1u, 128, 128);
+                for (int k = 0; k < (dim >> (kF8 ? 5 : 4)); ++k) {
                     const uint64_t dh = tc::smem_desc(tbase + k * 256, 128, SBO);
-                    tc::mma_bf16(taddr, dh, dh, idesc, k > 0 ? 1u : 0u);
-                    if (four) {
-                        const uint64_t dl = tc::smem_desc(tbase + region + k * 256, 128, SBO);
-                        tc::mma_bf16(taddr, dl, dh, idesc, 1u);
-                        tc::mma_bf16(taddr, dh, dl, idesc, 1u);
-                        tc::mma_bf16(taddr, dl, dl, idesc, 1u);
+                    const uint64_t dl = tc::smem_desc(tbase + region + k * 256, 128, SBO);
+                    if (kF8) {
+                        tc::mma_fp8(taddr, dh, dh, idesc, k > 0 ? 1u : 0u);
+                        if (four) {
+                            tc::mma_fp8(taddr, dl, dh, idesc, 1u);
+                            tc::mma_fp8(taddr, dh, dl, idesc, 1u);
+                            tc::mma_fp8(taddr, dl, dl, idesc, 1u);
+                        }
+                    } else {
+                        tc::mma_bf16(taddr, dh, dh, idesc, k > 0 ? 1u : 0u);
+                        if (four) {
+                            tc::mma_bf16(taddr, dl, dh, idesc, 1u);
+                            tc::mma_bf16(taddr, dh, dl, idesc, 1u);
+                            tc::mma_bf16(taddr, dl, dl, idesc, 1u);
+                        }
                     }
                 }
                 if (!a.test_withhold_commit) tc::mma_commit(&s.bar);
@@ -377,6 +536,7 @@ __global__ void __launch_bounds__(kQT) prune_pair_kernel(const PruneArgs a, int 
                     g = lane == q ? __uint_as_float(ra[q]) : g;
                     g = lane == q + 16 ? __uint_as_float(rb[q]) : g;
                 }
+                if (kF8) g *= isc_t * isc_t;   // exact: powers of two
                 gs = g;
                 ns2 = fmaxf(g, 0.f) * (1.0f + 2.0f * e1);
             }
@@ -414,7 +574,8 @@ __global__ void __launch_bounds__(kQT) prune_pair_kernel(const PruneArgs a, int 
 #pragma unroll
                     for (int q = 0; q < 16; ++q) {
                         const int c = c0 + q;
-                        const float g = __uint_as_float(rv[q]);
+                        float g = __uint_as_float(rv[q]);
+                        if (kF8) g *= isc_t * s.isc[o][c];   // exact: powers of two
                         const float2 pqc = s.pq[o][c];
                         const bool act = (a16 >> q) & 1u;
                         const float up = fmaf(m2a, g, pqc.x + As);
@@ -621,7 +782,9 @@ cudaError_t launch_pair_exact_check(const SegTable &t, int32_t dim, int32_t *scr
 }
 
 bool prune_pair_ok(int dim, int prec, int metric) {
-    return prec == 1 && metric == 0 && dim >= 16 && dim <= kQMaxDim && dim % 16 == 0;
+    if (metric != 0 || dim > kQMaxDim) return false;
+    if (prec == 1) return dim >= 16 && dim % 16 == 0;
+    return prec == 2 && dim >= 32 && dim % 32 == 0;   // E4M3: 32 elements per K-step
 }
 
 int prune_pair_max_pool() { return kQC; }
@@ -631,9 +794,10 @@ cudaError_t launch_prune_pair(const PruneArgs &in, cudaStream_t st) {
     PruneArgs a = in;
     // test-only: withhold the MMA completion signal, so every wait runs out
     a.test_withhold_commit = getenv("RNSM_TEST_WITHHOLD_COMMIT") != nullptr;
-    // hi (and lo) terms, 128 rows of 2 dim bytes each
-    const size_t dyn = (size_t)(a.pair_hi_only ? 256 : 512) * a.dim;
-    auto kern = a.pair_hi_only ? prune_pair_kernel<true> : prune_pair_kernel<false>;
+    // hi (and lo) terms, 128 rows of 2 dim bytes (BF16) or dim bytes (E4M3) each
+    const bool f8 = a.prec == 2;
+    const size_t dyn = (size_t)(f8 || a.pair_hi_only ? 256 : 512) * a.dim;
+    auto kern = f8 ? prune_pair_kernel<2> : a.pair_hi_only ? prune_pair_kernel<1> : prune_pair_kernel<0>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     if (e != cudaSuccess) return e;
     cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);

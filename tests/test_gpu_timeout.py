@@ -22,10 +22,10 @@ def rn():
     return rnsm
 
 
-# L2 at d = 64 with pools of 40: the two-owner pair tile; inner product: the
-# general tile (one owner per CTA)
-@pytest.mark.parametrize("metric", [0, 1])
-def test_tile_wait_runs_out_and_the_context_stays_usable(rn, monkeypatch, metric):
+# L2 at d = 64 with pools of 40: the two-owner pair tile (BF16 and FP8); inner
+# product: the general tile (one owner per CTA)
+@pytest.mark.parametrize("metric,prec", [(0, 1), (1, 1), (0, 2)])
+def test_tile_wait_runs_out_and_the_context_stays_usable(rn, monkeypatch, metric, prec):
     n = 2000
     X = torch.from_numpy(gen.gaussian(n, 64, 5)).cuda()
     if metric == 1:
@@ -36,9 +36,9 @@ def test_tile_wait_runs_out_and_the_context_stays_usable(rn, monkeypatch, metric
     want = rn.prune(X, owners, pool, 16, 1.2, metric=metric)
     monkeypatch.setenv("RNSM_TEST_WITHHOLD_COMMIT", "1")
     with pytest.raises(rn.RnsmError) as ei:
-        rn.prune(X, owners, pool, 16, 1.2, metric=metric, prec=rn.BF16)
+        rn.prune(X, owners, pool, 16, 1.2, metric=metric, prec=prec)
     assert ei.value.status == rn.ETIMEOUT
     monkeypatch.delenv("RNSM_TEST_WITHHOLD_COMMIT")
     torch.cuda.synchronize()          # no sticky error: the context still works
-    got = rn.prune(X, owners, pool, 16, 1.2, metric=metric, prec=rn.BF16)
+    got = rn.prune(X, owners, pool, 16, 1.2, metric=metric, prec=prec)
     assert torch.equal(got, want)
