@@ -107,6 +107,16 @@ typedef struct {
  * once the search launch shapes are autotuned and the plan's result tables
  * fit one group).  phase_ms[4] then holds S4 to S7 together. */
 #define RNSM_FLAG_GRAPH 0x4u
+/* Multi-pair union variant (not in the paper; for merging several pairs at
+ * once, e.g. several new partitions of an incremental merge): the searches
+ * of every plan edge as in Algorithm 2, then ONE prune per source vertex of
+ * its list and the first c_cross results of each of its plan edges (in plan
+ * order), then ONE reverse-edge pass over the kept cross edges of every
+ * source (a cross edge: one into a target segment of a plan edge of that
+ * source).  Every prune sees the lists as they were before the plan's reverse
+ * edges.  Needs the plan's result tables to fit one group (L * 4 bytes per
+ * source vertex per edge, 4 GiB in all); not combined with RNSM_FLAG_GRAPH. */
+#define RNSM_FLAG_UNION 0x8u
 
 /* One edge of a merge plan: segment `src` is merged into segment `dst`.
  * Plan order = array order (Section 5: closer pairs first). */

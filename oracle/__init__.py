@@ -82,7 +82,7 @@ def _declare(lib):
         "orc_build": (i32, [P, i64, i64, i32, i32, i32, f32, i64, P, P, i32]),
         "orc_bruteforce_knn": (i32, [P, i64, i64, i32, P, i64, i32, P, P, i32]),
         "orc_rnsm_merge": (i32, [P, i64, P, i32, P, i32, P, i32, i32, i32, f32, i32, i32, i32,
-                                 i32, P, P, i32, P, P, i32, i32]),
+                                 i32, P, P, i32, P, P, i32, i32, i32]),
         "orc_mos": (i32, [i32, P, i32, i32, P, P, P, P, i32]),
         "orc_mos_plan": (i32, [i32, P, P, i32, i32, i32, P, P, P, P, i32]),
     }
@@ -244,7 +244,7 @@ def bruteforce_knn(X, Q, k, metric=L2, threads=0):
 
 
 def rnsm_merge(segments, graphs, entries, plan, R, L, alpha, metric=L2, k_rev=5, k_plus=None,
-               ef_slide=None, c_cross=None, threads=0, cm=False):
+               ef_slide=None, c_cross=None, threads=0, cm=False, union_prune=False):
     """Algorithm 2 over the pairs of ``plan`` [(src, dst), ...] in order.
 
     segments: list of [n_s, d] float32; graphs: list of [n_s, r_in] int32
@@ -252,7 +252,10 @@ def rnsm_merge(segments, graphs, entries, plan, R, L, alpha, metric=L2, k_rev=5,
     graph [N, R] in global ids (segment-concatenation order) and stats.
     cm=True runs the Cross-query Merge comparator (Section 3.1) instead:
     every source vertex runs a naive search of the target (no expansion,
-    pivots or sliding), then the same prune and reverse edges."""
+    pivots or sliding), then the same prune and reverse edges.
+    union_prune=True runs the multi-pair union variant: the searches of every
+    plan edge, then one prune per source vertex over its list and the first
+    c_cross results of each of its edges, then one reverse-edge pass."""
     p = default_params(R, L, k_rev, k_plus, ef_slide, c_cross)
     X = _f32(np.concatenate(segments, axis=0))
     sizes = np.array([s.shape[0] for s in segments], np.int64)
@@ -267,7 +270,7 @@ def rnsm_merge(segments, graphs, entries, plan, R, L, alpha, metric=L2, k_rev=5,
     rc = _load().orc_rnsm_merge(_p(X), X.shape[1], _p(seg_off), len(segments), _p(adj), r_in,
                                 _p(ent), metric, R, L, alpha, p["k_rev"], p["k_plus"],
                                 p["ef_slide"], p["c_cross"], _p(ps), _p(pd), len(plan), _p(out),
-                                _p(st), threads, int(bool(cm)))
+                                _p(st), threads, int(bool(cm)), int(bool(union_prune)))
     _check(rc, "rnsm_merge")
     keys = ["ndc_expand", "ndc_search", "nexp_expand", "nexp_search", "pivots", "followers",
             "dependent_pivots", "reverse_edges"]

@@ -811,13 +811,21 @@ typedef struct {
  * vertex in the target, no expansion, pivots or sliding): S1-S3 are skipped,
  * every source vertex is a pivot and S4 runs for all of them; S6 and S7 as
  * for RNSM.
+ * union_prune != 0: the multi-pair union variant (not in the paper; the
+ * merge of several pairs at once, e.g. several new partitions of an
+ * incremental merge): S1-S5 of every plan edge as above, then ONE prune per
+ * source vertex of W = list(v) u the first c_cross results of each of its
+ * plan edges (blocks in plan order), then ONE reverse-edge pass over the kept
+ * cross edges of every source, a cross edge being one into a target segment
+ * of a plan edge of that source.  Every prune of the plan sees the lists as
+ * they were before the plan's reverse edges.
  */
 int32_t orc_rnsm_merge(const float *X, int64_t d, const int64_t *seg_off, int32_t m,
                        const int32_t *adj, int32_t r_in, const int32_t *entries, int32_t metric,
                        int32_t R, int32_t L, float alpha, int32_t k_rev, int32_t k_plus,
                        int32_t ef_slide, int32_t c_cross, const int32_t *plan_src,
                        const int32_t *plan_dst, int32_t n_plan, int32_t *out_adj, int64_t *stats,
-                       int32_t nthreads, int32_t cm) {
+                       int32_t nthreads, int32_t cm, int32_t union_prune) {
     if (m < 1 || R < 1 || L < 1 || r_in < 0 || r_in > R || k_rev < 1 || k_plus < k_rev ||
         ef_slide < 1 || ef_slide > L || c_cross < 1 || c_cross > ef_slide)
         return ORC_EINVAL;
@@ -849,11 +857,22 @@ int32_t orc_rnsm_merge(const float *X, int64_t d, const int64_t *seg_off, int32_
     int64_t *qidx = (int64_t *)malloc(sizeof(int64_t) * (size_t)nmax);
     int64_t *ndcb = (int64_t *)malloc(sizeof(int64_t) * (size_t)nmax);
     int64_t *nexb = (int64_t *)malloc(sizeof(int64_t) * (size_t)nmax);
+    /* union mode: plan edges of each source (E_s), the block of each edge in its
+     * source's union pool, and the pools themselves [n_s * E_s * c_cross] */
+    int32_t *n_edges = (int32_t *)calloc((size_t)m, sizeof(int32_t));
+    int32_t *blk = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n_plan > 0 ? n_plan : 1));
+    int32_t **upool = (int32_t **)calloc((size_t)m, sizeof(int32_t *));
     if (!Qb || !seedb || !resP || !resB || !W || !newl || !own || !eu || !ev || !qidx || !ndcb ||
-        !nexb) {
+        !nexb || !n_edges || !blk || !upool) {
         rc = ORC_ENOMEM;
         goto done;
     }
+    if (union_prune)
+        for (int32_t pi = 0; pi < n_plan; ++pi) {
+            int32_t s = plan_src[pi];
+            if (s < 0 || s >= m) { rc = ORC_EINVAL; goto done; }
+            blk[pi] = n_edges[s]++;
+        }
     for (int32_t pi = 0; pi < n_plan; ++pi) {
         int32_t s = plan_src[pi], t = plan_dst[pi];
         if (s < 0 || s >= m || t < 0 || t >= m || s == t) { rc = ORC_EINVAL; goto done; }
@@ -929,6 +948,21 @@ int32_t orc_rnsm_merge(const float *X, int64_t d, const int64_t *seg_off, int32_
             st[3] += nexb[i];
             memcpy(resP + qidx[i] * L, resB + i * ef_slide, sizeof(int32_t) * (size_t)ef_slide);
         }
+        if (union_prune) {
+            /* keep the first c_cross results (global ids) in this edge's block */
+            if (!upool[s]) {
+                upool[s] = (int32_t *)malloc(sizeof(int32_t) * (size_t)ns * (size_t)n_edges[s] *
+                                             (size_t)c_cross);
+                if (!upool[s]) { rc = ORC_ENOMEM; goto done; }
+            }
+            const int64_t w = (int64_t)n_edges[s] * c_cross;
+            for (int64_t v = 0; v < ns; ++v)
+                for (int32_t j = 0; j < c_cross; ++j) {
+                    int32_t u = resP[v * L + j];
+                    upool[s][v * w + (int64_t)blk[pi] * c_cross + j] = u >= 0 ? (int32_t)(u + t0) : -1;
+                }
+            continue;
+        }
         /* S6: source-side UpdateGraph: list(v) u first c_cross results, prune */
         int32_t wl = R + c_cross;
         for (int64_t v = 0; v < ns; ++v) {
@@ -957,6 +991,62 @@ int32_t orc_rnsm_merge(const float *X, int64_t d, const int64_t *seg_off, int32_
         rc = orc_reverse_edges(X, d, metric, out_adj, R, eu, ev, ne, alpha, nthreads);
         if (rc) goto done;
     }
+    if (union_prune && n_plan > 0) {
+        /* one prune per source vertex over its union pool, sources in order of
+         * their first plan edge; then one reverse-edge pass */
+        int64_t cap = 0;
+        for (int32_t s = 0; s < m; ++s)
+            if (n_edges[s]) cap += (seg_off[s + 1] - seg_off[s]) * R;
+        int32_t *Eu = (int32_t *)malloc(sizeof(int32_t) * (size_t)(cap > 0 ? cap : 1));
+        int32_t *Ev = (int32_t *)malloc(sizeof(int32_t) * (size_t)(cap > 0 ? cap : 1));
+        uint8_t *is_tgt = (uint8_t *)malloc((size_t)m);
+        int64_t ne = 0;
+        if (!Eu || !Ev || !is_tgt) rc = ORC_ENOMEM;
+        for (int32_t pi = 0; pi < n_plan && rc == ORC_OK; ++pi) {
+            int32_t s = plan_src[pi];
+            if (blk[pi] != 0) continue;   /* not the source's first edge */
+            int64_t s0 = seg_off[s], ns = seg_off[s + 1] - s0;
+            int64_t w = (int64_t)n_edges[s] * c_cross, wl = R + w;
+            int32_t *Wu = (int32_t *)malloc(sizeof(int32_t) * (size_t)(ns * wl));
+            int64_t *ow = (int64_t *)malloc(sizeof(int64_t) * (size_t)ns);
+            int32_t *nl = (int32_t *)malloc(sizeof(int32_t) * (size_t)(ns * R));
+            if (!Wu || !ow || !nl) {
+                rc = ORC_ENOMEM;
+            } else {
+                for (int64_t v = 0; v < ns; ++v) {
+                    ow[v] = s0 + v;
+                    memcpy(Wu + v * wl, out_adj + (s0 + v) * R, sizeof(int32_t) * (size_t)R);
+                    memcpy(Wu + v * wl + R, upool[s] + v * w, sizeof(int32_t) * (size_t)w);
+                }
+                rc = orc_prune_batch(X, d, metric, ow, ns, Wu, (int32_t)wl, R, alpha, 0, nl, NULL,
+                                     nthreads);
+            }
+            if (rc == ORC_OK) {
+                memset(is_tgt, 0, (size_t)m);
+                for (int32_t pj = 0; pj < n_plan; ++pj)
+                    if (plan_src[pj] == s) is_tgt[plan_dst[pj]] = 1;
+                for (int64_t v = 0; v < ns; ++v)
+                    for (int32_t j = 0; j < R; ++j) {
+                        int32_t u = nl[v * R + j];
+                        out_adj[(s0 + v) * R + j] = u;
+                        if (u < 0) continue;
+                        int32_t su = 0;   /* segment of u */
+                        while (seg_off[su + 1] <= u) ++su;
+                        if (is_tgt[su]) {
+                            Eu[ne] = u;
+                            Ev[ne] = (int32_t)(s0 + v);
+                            ++ne;
+                        }
+                    }
+            }
+            free(Wu); free(ow); free(nl);
+        }
+        if (rc == ORC_OK) {
+            st[7] += ne;
+            rc = orc_reverse_edges(X, d, metric, out_adj, R, Eu, Ev, ne, alpha, nthreads);
+        }
+        free(Eu); free(Ev); free(is_tgt);
+    }
 done:
     if (stats) memcpy(stats, st, sizeof(st));
     for (int32_t s = 0; s < m; ++s) {
@@ -966,6 +1056,9 @@ done:
     free(cache);
     free(Qb); free(seedb); free(resP); free(resB); free(W); free(newl); free(own); free(eu);
     free(ev); free(qidx); free(ndcb); free(nexb);
+    if (upool)
+        for (int32_t s = 0; s < m; ++s) free(upool[s]);
+    free(upool); free(n_edges); free(blk);
     return rc;
 }
 

@@ -811,15 +811,21 @@ struct MergeBufs {
     void *piv_tmp;
     int32_t *res;                          // [res_rows * L]
     int32_t *eu, *ev;
+    int32_t *upool;                        // union variant: the pools of one source
     SearchJob *jobs1, *jobs4, *jobs5;
     unsigned long long *rev_counts;        // [plan edges] kept cross edges per edge
     RevBufs rev;
     QuantBufs qb;
 };
 
+// e_max: the most plan edges of one source (sizes the union variant's pools).
 void carve_merge(Bump &b, const rnsm_params &p, int64_t nmax, int64_t n_all, int64_t res_rows,
-                 int32_t n_jobs, int32_t dim, int32_t qprec, Ctl &c, MergeBufs &m) {
-    take_ctl(b, c, nmax);
+                 int32_t n_jobs, int32_t dim, int32_t qprec, Ctl &c, MergeBufs &m,
+                 int32_t e_max = 1) {
+    const bool uni = (p.flags & RNSM_FLAG_UNION) != 0;
+    // the union variant prunes the targets of all sources in one pass
+    const int64_t nrev = uni ? n_all : nmax;
+    take_ctl(b, c, nrev);
     m.nplus = b.take<int32_t>(n_all * p.k_plus);
     m.rk_keys = b.take<int32_t>(nmax * p.k_rev);
     m.rk_vals = b.take<int32_t>(nmax * p.k_rev);
@@ -835,13 +841,14 @@ void carve_merge(Bump &b, const rnsm_params &p, int64_t nmax, int64_t n_all, int
     m.rank = b.take<int32_t>(n_all);
     m.piv_tmp = b.take<char>(pivot_tmp_bytes(nmax));
     m.res = b.take<int32_t>(res_rows * p.L);
-    m.eu = b.take<int32_t>(nmax * p.R);
-    m.ev = b.take<int32_t>(nmax * p.R);
+    m.eu = b.take<int32_t>(nrev * p.R);
+    m.ev = b.take<int32_t>(nrev * p.R);
+    m.upool = uni ? b.take<int32_t>(nmax * (int64_t)e_max * p.c_cross) : nullptr;
     m.jobs1 = b.take<SearchJob>(n_jobs + 1);
     m.jobs4 = b.take<SearchJob>(n_jobs + 1);
     m.jobs5 = b.take<SearchJob>(n_jobs + 1);
     m.rev_counts = b.take<unsigned long long>(n_jobs + 1);
-    take_rev(b, nmax, nmax * p.R, m.rev);
+    take_rev(b, nrev, nrev * p.R, m.rev);
     take_quant(b, n_all, dim, qprec, p.metric, m.qb);
 }
 
@@ -991,7 +998,8 @@ size_t rnsm_workspace_size(const rnsm_segment *segs, int32_t m, const rnsm_param
     Bump b;
     Ctl c;
     MergeBufs mb;
-    carve_merge(b, p, nmax, nall, res_rows, m * (m > 1 ? m - 1 : 1), segs[0].dim, qprec, c, mb);
+    carve_merge(b, p, nmax, nall, res_rows, m * (m > 1 ? m - 1 : 1), segs[0].dim, qprec, c, mb,
+                m > 1 ? m - 1 : 1);
     return b.off;
 }
 
@@ -1027,12 +1035,22 @@ rnsm_status rnsm_merge(const rnsm_segment *segs, int32_t m, const rnsm_params *p
     const int32_t qprec = prune_tc_terms(dim, p.prec) ? p.prec : 0;  // else FP32 kernels
     const int64_t res_rows = plan_res_rows(segs, pl, p.L);
     const int32_t n_jobs = (int32_t)pl.size() > m ? (int32_t)pl.size() : m;
+    int32_t e_max = 1;
+    {
+        std::vector<int32_t> ne((size_t)m, 0);
+        for (const PlanEdge &e : pl) e_max = std::max(e_max, ++ne[(size_t)e.src]);
+    }
+    const bool uni = (p.flags & RNSM_FLAG_UNION) != 0;
+    if (uni && (p.flags & RNSM_FLAG_GRAPH))
+        return fail(RNSM_EINVAL, "RNSM_FLAG_UNION does not combine with RNSM_FLAG_GRAPH");
+    if (uni && res_rows < [&] { int64_t t = 0; for (const PlanEdge &e : pl) t += segs[e.src].n; return t; }())
+        return fail(RNSM_EINVAL, "RNSM_FLAG_UNION needs the plan's search results in one group");
     Bump b;
     Ctl c;
     MergeBufs mb;
-    carve_merge(b, p, nmax, off, res_rows, n_jobs, dim, qprec, c, mb);
+    carve_merge(b, p, nmax, off, res_rows, n_jobs, dim, qprec, c, mb, e_max);
     TRY(ws_acquire(b.off, b));
-    carve_merge(b, p, nmax, off, res_rows, n_jobs, dim, qprec, c, mb);
+    carve_merge(b, p, nmax, off, res_rows, n_jobs, dim, qprec, c, mb, e_max);
     TRY(ctl_reset(c, st));
     for (int32_t s = 0; s < m; ++s)
         TRY(validate_on_device(segs[s].vecs, segs[s].n, dim, segs[s].adj, segs[s].r_in, c, st));
@@ -1233,6 +1251,60 @@ rnsm_status rnsm_merge(const rnsm_segment *segs, int32_t m, const rnsm_params *p
             TRY(run_search(a, c.work + 3, es));
         }
         tm.end(span);
+        if (uni) {
+            // one prune per source vertex over its union pool, sources in order of
+            // their first plan edge; then the kept cross edges of every source and
+            // one reverse-edge pass over all ids
+            span = graph ? -1 : tm.begin(6);
+            UnionMasks mk;
+            std::memset(&mk, 0, sizeof(mk));
+            for (size_t e = g0; e < g1; ++e) mk.tmask[pl[e].src] |= 1ull << pl[e].dst;
+            std::vector<char> done((size_t)m, 0);
+            for (size_t e0 = g0; e0 < g1; ++e0) {
+                const int32_t sv = pl[e0].src;
+                if (done[(size_t)sv]) continue;
+                done[(size_t)sv] = 1;
+                UnionEdges ue;
+                std::memset(&ue, 0, sizeof(ue));
+                for (size_t e = e0; e < g1; ++e)
+                    if (pl[e].src == sv) {
+                        ue.res[ue.n] = mb.res + res_off[e] * p.L;
+                        ue.t0[ue.n] = (int32_t)tab.off[pl[e].dst];
+                        ++ue.n;
+                    }
+                const int64_t ns = segs[sv].n;
+                CK(launch_union_pool(ue, ns, p.L, p.c_cross, mb.upool, es));
+                PruneArgs q = prune_defaults();
+                q.segs = tab;
+                q.dim = dim;
+                q.metric = p.metric;
+                q.alpha = p.alpha;
+                q.R = p.R;
+                q.n_owners = ns;
+                q.owner_base = (int32_t)tab.off[sv];
+                q.listA = out_adj;
+                q.lenA = p.R;
+                q.listB = mb.upool;
+                q.strideB = ue.n * p.c_cross;
+                q.lenB = ue.n * p.c_cross;
+                q.offB = 0;
+                q.out = out_adj;
+                q.err = c.err;
+                apply_quant(q, &mb.qb, c.rechecks, c.tile_err);
+                TRY(run_prune(q, c.work + 8, c, es));
+            }
+            tm.end(span);
+            span = graph ? -1 : tm.begin(7);
+            CK(cudaMemsetAsync(c.ecount, 0, sizeof(unsigned long long), es));
+            CK(launch_emit_cross(out_adj, p.R, tab, mk, mb.eu, mb.ev, c.ecount, es));
+            TRY(reverse_into(tab, dim, p, out_adj, mb.eu, mb.ev, tab.off[m] * p.R, c.ecount, 0,
+                             tab.off[m], -1, mb.rev, c, es, &mb.qb));
+            CK(cudaMemsetAsync(mb.rev_counts + g0, 0, sizeof(unsigned long long) * (g1 - g0), es));
+            CK(cudaMemcpyAsync(mb.rev_counts + g0, c.ecount, sizeof(unsigned long long),
+                               cudaMemcpyDeviceToDevice, es));
+            tm.end(span);
+            return RNSM_OK;
+        }
         for (size_t e = g0; e < g1; ++e) {   // S6 and S7 per edge, in plan order
             const PlanEdge &E = pl[e];
             const int64_t ns = segs[E.src].n, nt = segs[E.dst].n;
@@ -1277,7 +1349,7 @@ rnsm_status rnsm_merge(const rnsm_segment *segs, int32_t m, const rnsm_params *p
         std::vector<SearchJob> j4 = jobs_of(groups[gi].first, groups[gi].second, false, tot4);
         std::vector<SearchJob> j5 = jobs_of(groups[gi].first, groups[gi].second, true, tot5);
         // capture only what replays unchanged: one group, no autotuning inside
-        const bool want_graph = (p.flags & RNSM_FLAG_GRAPH) && groups.size() == 1 &&
+        const bool want_graph = (p.flags & RNSM_FLAG_GRAPH) && !uni && groups.size() == 1 &&
                                 !search_would_tune(dim, p.L, kSeedConst, tot4) &&
                                 !search_would_tune(dim, p.ef_slide, kSeedTable, tot5);
         TRY(upload_jobs(j4, tot4, mb.jobs4, st));

@@ -152,6 +152,23 @@ cudaError_t launch_pair_exact_check(const SegTable &t, int32_t dim, int32_t *scr
 cudaError_t launch_quantize(const SegTable &segs, int64_t n, int32_t dim, int prec, void *q,
                             void *q_lo, float *scale, float *err, float *norm, cudaStream_t st);
 
+// The multi-pair union variant (union.cu).  UnionEdges: the plan edges of one
+// source, in plan order: result rows (by local source vertex, L wide, local
+// target ids) and the global offset of each target.  UnionMasks: per segment,
+// the bit set of its targets (0: not a source of the plan).
+struct UnionEdges {
+    const int32_t *res[kMaxSeg];
+    int32_t t0[kMaxSeg];
+    int32_t n;
+};
+struct UnionMasks {
+    unsigned long long tmask[kMaxSeg];
+};
+cudaError_t launch_union_pool(const UnionEdges &e, int64_t ns, int32_t L, int32_t c, int32_t *pool,
+                              cudaStream_t st);
+cudaError_t launch_emit_cross(const int32_t *lists, int32_t R, const SegTable &t, const UnionMasks &mk,
+                              int32_t *eu, int32_t *ev, unsigned long long *count, cudaStream_t st);
+
 // Query schedule (schedule.cu).  launch_locality_order: the n rows of x
 // counting-sorted by a random-hyperplane locality key (order) and each row's
 // position in that order (rank); keys, vals: n scratch entries each; offs,

@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(kThreads) prune_kernel(const PruneArgs a, int 
     __shared__ int64_t sh_i;  // first owner of the claimed chunk
     __shared__ int sh_np, sh_nk, sh_ebase;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int dim = a.dim, F4 = dim >> 2;
+    const int dim = a.dim;
     const int R = a.R;
     const int metric = a.metric;
 

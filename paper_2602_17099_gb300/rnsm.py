@@ -24,6 +24,7 @@ FP32, BF16, FP8 = 0, 1, 2
 FLAG_CM = 0x1
 FLAG_HOST_PIVOTS = 0x2
 FLAG_GRAPH = 0x4
+FLAG_UNION = 0x8
 _STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "EGRAPH"}
 
 

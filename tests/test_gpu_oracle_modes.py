@@ -126,3 +126,40 @@ def test_cm_comparator_exact_on_integer_data(rn, plan):
         np.testing.assert_array_equal(host(got), want)
         assert gst["pivots"] == wst["pivots"] and gst["followers"] == 0
         assert gst["reverse_edges"] == wst["reverse_edges"]
+
+
+@pytest.mark.parametrize("cm", [False, True])
+def test_union_prune_exact_on_integer_data(rn, cm):
+    # the multi-pair union variant: a source with three edges, a segment that is
+    # source and target, a target reached from two sources; pools of up to
+    # R + 3 c_cross = 64 candidates (small kernels) and, at c_cross 32, 112
+    sizes = [1600, 700, 900, 500]
+    segs = [gen.sift_like(n, 160 + i, d=64) for i, n in enumerate(sizes)]
+    gs = [oracle.build_graph(s, 16, 32, 1.2) for s in segs]
+    graphs, entries = [g for g, _ in gs], [e for _, e in gs]
+    plan = [(3, 0), (1, 0), (3, 2), (2, 0), (3, 1)]
+    tsegs = [(dev(s), dev(g), e) for s, g, e in zip(segs, graphs, entries)]
+    flags = rn.FLAG_UNION | (rn.FLAG_CM if cm else 0)
+    for c_cross in (16, 32):
+        want, wst = oracle.rnsm_merge(segs, graphs, entries, plan, 16, 32, 1.2, cm=cm,
+                                      union_prune=True, ef_slide=32, c_cross=c_cross)
+        for prec in (rn.FP32, rn.BF16):
+            got, gst = rn.merge(tsegs, rn.params(16, 32, 1.2, prec=prec, flags=flags,
+                                                 ef_slide=32, c_cross=c_cross),
+                                [(a, b, 0.0) for a, b in plan])
+            np.testing.assert_array_equal(host(got), want)
+            assert gst["reverse_edges"] == wst["reverse_edges"]
+            assert gst["pivots"] == wst["pivots"] and gst["followers"] == wst["followers"]
+
+
+def test_union_incremental_step_against_oracle(rn):
+    # one step of the incremental scenario with three new partitions merged into
+    # the index at once: each into the index, and the later ones into the earlier
+    parts = [gen.sift_like(n, 170 + i, d=32) for i, n in enumerate([2000, 600, 600, 600])]
+    gs = [oracle.build_graph(s, 12, 24, 1.2) for s in parts]
+    plan = [(1, 0), (2, 0), (3, 0), (2, 1), (3, 1), (3, 2)]
+    want, _ = oracle.rnsm_merge(parts, [g for g, _ in gs], [e for _, e in gs], plan, 12, 24, 1.2,
+                                union_prune=True)
+    got, _ = rn.merge([(dev(s), dev(g), e) for s, (g, e) in zip(parts, gs)],
+                      rn.params(12, 24, 1.2, flags=rn.FLAG_UNION), [(a, b, 0.0) for a, b in plan])
+    np.testing.assert_array_equal(host(got), want)

@@ -632,3 +632,69 @@ def test_cm_merge_equals_its_pinned_parts():
     assert rst["followers"] > 0
     assert not np.array_equal(rn_out, oracle.rnsm_merge(segs, graphs, entries, [(1, 0)], 8, 16,
                                                          1.2, cm=True)[0])
+
+
+def _union_cm_by_parts(segs, graphs, entries, plan, R, L, alpha, c_cross):
+    """The multi-pair union variant with CM searches, from the pinned parts:
+    every source vertex searches the frozen graph of each target of its plan
+    edges (naive beam search from the target's entry, ef = L); one prune per
+    source vertex over its list and the first c_cross results of each edge
+    (blocks in plan order); then one reverse-edge pass over the kept edges
+    into targets of the vertex's own plan edges."""
+    X = np.concatenate(segs)
+    off = np.concatenate([[0], np.cumsum([len(s) for s in segs])])
+    lists = np.full((len(X), R), -1, np.int32)
+    for s, g in enumerate(graphs):
+        lists[off[s]:off[s + 1], :g.shape[1]] = np.where(g >= 0, g + off[s], -1)
+    blocks = {}
+    for s, t in plan:
+        seeds = np.full((len(segs[s]), 1), entries[t], np.int32)
+        res, _, _, _, _ = oracle.beam_search(segs[t], graphs[t], segs[s], seeds, L, L)
+        blocks.setdefault(s, []).append(np.where(res[:, :c_cross] >= 0,
+                                                 res[:, :c_cross] + off[t], -1))
+    eu, ev = [], []
+    for s in dict.fromkeys(s for s, _ in plan):
+        owners = np.arange(off[s], off[s + 1], dtype=np.int64)
+        pool = np.concatenate([lists[off[s]:off[s + 1]]] + blocks[s], axis=1).astype(np.int32)
+        new, _ = oracle.prune(X, owners, pool, R, alpha)
+        lists[off[s]:off[s + 1]] = new
+        tgts = {t for s2, t in plan if s2 == s}
+        seg_of = np.searchsorted(off, np.arange(len(X)), side="right") - 1
+        for i, v in enumerate(owners):
+            for u in new[i]:
+                if u >= 0 and seg_of[u] in tgts:
+                    eu.append(u)
+                    ev.append(v)
+    return oracle.reverse_edges(X, lists, np.array(eu, np.int32), np.array(ev, np.int32), alpha)
+
+
+def test_union_prune_equals_its_pinned_parts():
+    # with CM searches the union variant is a composition of pinned parts; the
+    # plan has a source with three edges, a segment that is source and target,
+    # and a target reached from two sources
+    segs = [gen.gaussian(400, 8, 140), gen.gaussian(250, 8, 141), gen.gaussian(200, 8, 142),
+            gen.gaussian(150, 8, 143)]
+    gs = [oracle.build_graph(s, 8, 16, 1.2) for s in segs]
+    graphs, entries = [g for g, _ in gs], [e for _, e in gs]
+    plan = [(3, 0), (1, 0), (3, 2), (2, 0), (3, 1)]
+    got, st = oracle.rnsm_merge(segs, graphs, entries, plan, 8, 16, 1.2, cm=True,
+                                union_prune=True)
+    want = _union_cm_by_parts(segs, graphs, entries, plan, 8, 16, 1.2, c_cross=8)
+    np.testing.assert_array_equal(got, want)
+    # it is not the edge-by-edge merge
+    seq, _ = oracle.rnsm_merge(segs, graphs, entries, plan, 8, 16, 1.2, cm=True)
+    assert not np.array_equal(got, seq)
+
+
+def test_union_prune_with_one_edge_per_disjoint_pair_is_the_pairwise_merge():
+    # each source one edge, no segment both source and target, distinct
+    # targets: one prune per vertex and one reverse pass are the pairwise merges
+    segs = [gen.gaussian(300, 8, 150), gen.gaussian(200, 8, 151), gen.gaussian(260, 8, 152),
+            gen.gaussian(180, 8, 153)]
+    gs = [oracle.build_graph(s, 8, 16, 1.2) for s in segs]
+    graphs, entries = [g for g, _ in gs], [e for _, e in gs]
+    plan = [(1, 0), (3, 2)]
+    a, sa = oracle.rnsm_merge(segs, graphs, entries, plan, 8, 16, 1.2, union_prune=True)
+    b, sb = oracle.rnsm_merge(segs, graphs, entries, plan, 8, 16, 1.2)
+    np.testing.assert_array_equal(a, b)
+    assert sa == sb
