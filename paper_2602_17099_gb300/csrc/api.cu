@@ -140,12 +140,12 @@ void take_quant(Bump &b, int64_t n, int32_t dim, int32_t prec, int32_t metric, Q
     qb.q = nullptr;
     qb.qlo = nullptr;
     if (prec == 0) return;
-    const int terms = prune_tc_terms(dim, prec);
+    const int terms = prune_tc_terms(dim, prec, metric);
     // L2 two-term tiles and the small-pool pair tiles centre the FP32 rows on
     // each owner; they store nothing
     if ((terms == 2 && metric == RNSM_METRIC_L2) || prune_pair_ok(dim, prec, metric)) return;
     qb.q = b.take<char>((size_t)n * dim * (prec == 2 ? 1 : 2));
-    if (terms == 2) qb.qlo = b.take<char>((size_t)n * dim * 2);
+    if (terms == 2) qb.qlo = b.take<char>((size_t)n * dim * (prec == 2 ? 1 : 2));
     qb.scale = b.take<float>(n);
     qb.err = b.take<float>(n);
     qb.norm = b.take<float>(n);

@@ -131,7 +131,9 @@ cudaError_t launch_prune(const PruneArgs &a, cudaStream_t st);
 // prune_tc_max_pool() raw candidates.  prune_tc_terms: 0 if (dim, prec) has no
 // tensor-core tile, 1 if it stages the quantized rows (qrows, qscale, qerr,
 // qnorm), 2 if it stages the FP32 rows split into two BF16 terms.
-int prune_tc_terms(int dim, int prec);
+// With the metric known, FP8 at inner product from d = 384 stages two E4M3
+// terms (hi, lo, stored by launch_quantize with q_lo).
+int prune_tc_terms(int dim, int prec, int metric = -1);
 int prune_tc_max_pool();
 cudaError_t launch_prune_tc(const PruneArgs &a, cudaStream_t st, int terms = 0);  // 0: prune_tc_terms
 // BF16 tensor-core prune of small pools, two owners per tile (L2, dim a
@@ -147,8 +149,9 @@ cudaError_t launch_pair_exact_check(const SegTable &t, int32_t dim, int32_t *scr
                                     cudaStream_t st);
 // Rows of the segment table to BF16 (prec 1) or E4M3 with per-row scale (prec 2),
 // plus residual norms and row norms.
-// With q_lo (BF16 only) the rows are split into q = bf16(x) and q_lo = bf16(x - q)
-// and err is ||x - q - q_lo||.
+// With q_lo the rows are split into two terms, q = bf16(x) and q_lo = bf16(x - q),
+// or for E4M3 q = e4m3(x / s) and q_lo = e4m3(x / s - q), and err is the norm of
+// what is left.
 cudaError_t launch_quantize(const SegTable &segs, int64_t n, int32_t dim, int prec, void *q,
                             void *q_lo, float *scale, float *err, float *norm, cudaStream_t st);
 

@@ -823,8 +823,11 @@ cudaError_t launch_prune(const PruneArgs &a, cudaStream_t st) {
     const bool pair = pair_ok && a.lenA + a.lenB <= prune_pair_max_pool();
     const int terms = pair ? 0
                       : pair_ok ? (a.prec == 1 ? 2 : 0)
-                      : a.prec != 0 ? prune_tc_terms(a.dim, a.prec) : 0;
-    const bool tc = terms == 2 || (terms == 1 && a.qrows);
+                      : a.prec != 0 ? prune_tc_terms(a.dim, a.prec, a.metric) : 0;
+    // two BF16 terms split the FP32 rows in the tile at L2; every other tile
+    // stages the library's stored terms
+    const bool tc = (terms == 2 && ((a.prec == 1 && a.metric == 0) || (a.qrows && a.qrows_lo))) ||
+                    (terms == 1 && a.qrows);
     const int cap = pair ? prune_pair_max_pool() : tc ? prune_tc_max_pool() : kSmallMax;
     const bool small_ok = a.ovf_list && a.ovf_count && a.work2 && a.lenA + a.lenB <= cap;
     if (!small_ok) return launch_general(a, nullptr, nullptr, st);

@@ -85,6 +85,7 @@ constexpr int kQCols = 128;        // TMEM columns (N = 128)
 constexpr int kQMaxDim = 128;
 constexpr uint64_t kQWaitNs = 1000000000ull;   // an MMA group takes microseconds
 constexpr int kQErrEvery = 256;    // owners between two tile-error samples (FP64 is slow here)
+constexpr int kQOpen = 64;         // open tests a warp queues per owner before deciding inline
 
 struct PairSmem {
     alignas(16) float vrow[2][kQMaxDim];   // the owners' FP32 rows
@@ -97,6 +98,8 @@ struct PairSmem {
     float2 pq[2][kQC];                     // column terms of the occlusion test
     float isc[2][kQC];                     // FP8: 1 / sigma of each slot's staged row
     uint32_t occ[2][kQC][2];               // occluders of slot c, by slot
+    uint2 open_q[4][kQOpen];               // per warp: tests the loose bound left open
+                                           // (tile value, c | slot << 8)
     uint32_t live[2][2];                   // valid slots (ids not repeated), per warp
     uint64_t bar;
     uint32_t tmem_slot;
@@ -163,7 +166,7 @@ __device__ __forceinline__ float e4m3_scale(float m) {
 // before the launch), so y = x_c - x_v is exact in FP32 and in BF16 (half the
 // shared memory); 2: two E4M3 terms with per-row power-of-two scales.
 template <int kKind>
-__global__ void __launch_bounds__(kQT) prune_pair_kernel(const PruneArgs a, int chunk) {
+__global__ void __launch_bounds__(kQT, 4) prune_pair_kernel(const PruneArgs a, int chunk) {
     constexpr bool kHiOnly = kKind == 1;
     constexpr bool kF8 = kKind == 2;
     extern __shared__ __align__(1024) unsigned char tile[];
@@ -564,6 +567,10 @@ __global__ void __launch_bounds__(kQT) prune_pair_kernel(const PruneArgs a, int 
                 // the live slots c after this lane's slot s in the order, if s is live
                 const uint64_t am = valid_t ? live & ~ltm & ~(1ull << p) : 0ull;
                 const float m2a = -2.0f * alpha;
+                // tests the loose bound leaves open are queued and decided after the
+                // loop, a lane per test (they are rare: inline, one lane's FP32
+                // distance would hold up the whole warp for each)
+                int nq = 0;
                 for (int ch = 0; ch < 4; ++ch) {
                     const int c0 = 16 * ch;
                     const uint32_t a16 = (uint32_t)(am >> c0) & 0xffffu;
@@ -581,15 +588,33 @@ __global__ void __launch_bounds__(kQT) prune_pair_kernel(const PruneArgs a, int 
                         const float up = fmaf(m2a, g, pqc.x + As);
                         const float dn = fmaf(m2a, g, pqc.y + As2);
                         bool occl = act && up < 0.f;
-                        if (act && !(up < 0.f) && !(dn > 0.f)) {
-                            const int res = decide_open(g, gs, ns2, s.gd[o][c], s.nn[o][c], s.sd[o][c],
-                                                        xrow, s.rp[o][c], dim, alpha, e1, kE, gam);
-                            occl = res & 1;
-                            rechecks += (unsigned long long)(res >> 1);
+                        const bool open = act && !(up < 0.f) && !(dn > 0.f);
+                        const unsigned om = __ballot_sync(0xffffffffu, open);
+                        if (open) {
+                            const int k = nq + __popc(om & lanemask_lt());
+                            if (k < kQOpen) {
+                                s.open_q[warp][k] = make_uint2(__float_as_uint(g), (uint32_t)c | ((uint32_t)p << 8));
+                            } else {
+                                const int res = decide_open(g, gs, ns2, s.gd[o][c], s.nn[o][c], s.sd[o][c],
+                                                            xrow, s.rp[o][c], dim, alpha, e1, kE, gam);
+                                occl = res & 1;
+                                rechecks += (unsigned long long)(res >> 1);
+                            }
                         }
+                        nq += __popc(om);
                         const unsigned m = __ballot_sync(0xffffffffu, occl);
                         if (lane == 0) s.occ[o][c][h] = m;
                     }
+                }
+                __syncwarp();
+                for (int k = lane; k < min(nq, kQOpen); k += 32) {
+                    const uint2 e = s.open_q[warp][k];
+                    const int c = (int)(e.y & 0xffu), ps = (int)(e.y >> 8);
+                    const int res = decide_open(__uint_as_float(e.x), s.gd[o][ps], s.nn[o][ps], s.gd[o][c],
+                                                s.nn[o][c], s.sd[o][c], s.rp[o][ps], s.rp[o][c], dim, alpha,
+                                                e1, kE, gam);
+                    rechecks += (unsigned long long)(res >> 1);
+                    if (res & 1) atomicOr(&s.occ[o][c][h], 1u << (ps & 31));
                 }
             }
             tc::fence_before_sync();

@@ -115,7 +115,7 @@ static_assert(offsetof(TcSmem, rptr) % 8 == 0 && offsetof(TcSmem, bar) % 8 == 0,
 
 template <bool kFp8, int kTerms>
 __global__ void __launch_bounds__(kThreads, 2) prune_tc_kernel(const PruneArgs a, int chunk) {
-    static_assert(kTerms == 1 || !kFp8, "the split tile is BF16");
+    // (two E4M3 terms only as the library's stored rows: inner product)
     // dynamic shared memory: the tile (kTerms regions of kN rows x kChunkB / kTerms
     // bytes), then two raw buffers of kRawRows rows x kChunkB bytes
     extern __shared__ __align__(1024) unsigned char tile[];
@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(kThreads, 2) prune_tc_kernel(const PruneArgs a
     const int metric = a.metric;
     const float alpha = a.alpha;
     // source rows: the quantized copies (one term) or the FP32 rows (two terms)
-    const int src_bytes = kTerms == 2 ? dim * 4 : dim * (kFp8 ? 1 : 2);
+    const int src_bytes = kTerms == 2 ? dim * (kFp8 ? 2 : 4) : dim * (kFp8 ? 1 : 2);
     const int n_chunks = (src_bytes + kChunkB - 1) / kChunkB;
     constexpr int kTermB = kChunkB / kTerms;        // tile bytes per row, term and chunk
     constexpr int kSBO = 8 * kTermB;                // bytes between core matrices along M/N
@@ -196,6 +196,12 @@ __global__ void __launch_bounds__(kThreads, 2) prune_tc_kernel(const PruneArgs a
                 const uint32_t acc = (kc > 0 || k > 0) ? 1u : 0u;
                 if (kFp8) {
                     tc::mma_fp8(taddr, dh, dh, idesc, acc);
+                    if (kTerms == 2) {
+                        const uint64_t dl = tc::smem_desc(tb + kRegion + k * 256, 128, kSBO);
+                        tc::mma_fp8(taddr, dl, dh, idesc, 1u);   // lo * hi
+                        tc::mma_fp8(taddr, dh, dl, idesc, 1u);   // hi * lo
+                        tc::mma_fp8(taddr, dl, dl, idesc, 1u);   // lo * lo
+                    }
                 } else {
                     tc::mma_bf16(taddr, dh, dh, idesc, acc);
                     if (kTerms == 2) {
@@ -257,7 +263,7 @@ __global__ void __launch_bounds__(kThreads, 2) prune_tc_kernel(const PruneArgs a
         }
         if (tid == 0) s.n_undecided = 0;
         __syncthreads();
-        if (kTerms == 1) {
+        if (kTerms == 1 || kFp8) {
             for (int r = tid; r <= kMaxC; r += kThreads) {
                 const bool own = r == kMaxC;
                 const int32_t g = own ? owner : (r < nc ? s.pid[r] : -1);
@@ -802,8 +808,9 @@ __global__ void __launch_bounds__(kThreads, 2) prune_tc_kernel(const PruneArgs a
 
 // Row quantisation: BF16 (round to nearest) or E4M3 with a per-row scale
 // (max |x| / 448), the residual norm ||x - x~|| (rounded up) and ||x||.  With
-// kSplit (BF16) the row is stored as hi = bf16(x) and lo = bf16(x - hi) and
-// the residual is ||x - hi - lo||.
+// kSplit the row is stored as hi = bf16(x) and lo = bf16(x - hi), or for E4M3
+// hi = e4m3(x / s) and lo = e4m3(x / s - hi), and the residual is what the two
+// terms leave (||x - hi - lo||, ||x - s (hi + lo)||).
 template <bool kFp8, bool kSplit>
 __global__ void quantize_kernel(SegTable segs, int64_t n, int32_t dim, void *q, void *q_lo,
                                 float *scale, float *err, float *norm) {
@@ -829,9 +836,16 @@ __global__ void quantize_kernel(SegTable segs, int64_t n, int32_t dim, void *q, 
             const float v = x[k];
             float dlt;
             if (kFp8) {
-                const __nv_fp8_e4m3 t(v / sc);
+                const float z = v / sc;
+                const __nv_fp8_e4m3 t(z);
                 reinterpret_cast<__nv_fp8_e4m3 *>(q)[r * dim + k] = t;
-                dlt = v - sc * static_cast<float>(t);
+                if (kSplit) {
+                    const __nv_fp8_e4m3 t2(z - static_cast<float>(t));
+                    reinterpret_cast<__nv_fp8_e4m3 *>(q_lo)[r * dim + k] = t2;
+                    dlt = v - sc * (static_cast<float>(t) + static_cast<float>(t2));
+                } else {
+                    dlt = v - sc * static_cast<float>(t);
+                }
             } else {
                 const __nv_bfloat16 t = __float2bfloat16_rn(v);
                 reinterpret_cast<__nv_bfloat16 *>(q)[r * dim + k] = t;
@@ -887,10 +901,13 @@ cudaError_t launch_tc(const PruneArgs &a, cudaStream_t st) {
 
 }  // namespace
 
-int prune_tc_terms(int dim, int prec) {
+int prune_tc_terms(int dim, int prec, int metric) {
     if (prec != 1 && prec != 2) return 0;
     if (dim < 16 || dim > 1024) return 0;
-    if (prec == 2) return dim % 32 == 0 ? 1 : 0;   // E4M3: 32 bytes per MMA K-step
+    if (prec == 2) {   // E4M3: 32 bytes per MMA K-step; two stored terms at IP from d = 384
+        if (dim % 32) return 0;
+        return metric == 1 && dim >= 384 ? 2 : 1;
+    }
     if (dim % 16) return 0;                        // BF16: 32 bytes per MMA K-step
     // the split tile costs twice the staged bytes; it pays where the one-term
     // bound (growing with the dimension) would send many tests to FP32
@@ -900,13 +917,14 @@ int prune_tc_terms(int dim, int prec) {
 int prune_tc_max_pool() { return kMaxC; }
 
 cudaError_t launch_prune_tc(const PruneArgs &in, cudaStream_t st, int terms) {
-    if (terms == 0) terms = prune_tc_terms(in.dim, in.prec);
-    if (terms == 0 || (terms == 2 && in.prec != 1)) return cudaErrorInvalidValue;
+    if (terms == 0) terms = prune_tc_terms(in.dim, in.prec, in.metric);
+    if (terms == 0 || (terms == 2 && in.prec == 2 && !(in.metric == 1 && in.qrows_lo)))
+        return cudaErrorInvalidValue;
     PruneArgs a = in;
     // test-only: withhold the MMA completion signal, so every wait runs out
     // and the launch ends with the timeout bit of the error word
     a.test_withhold_commit = getenv("RNSM_TEST_WITHHOLD_COMMIT") != nullptr;
-    if (a.prec == 2) return launch_tc<true, 1>(a, st);
+    if (a.prec == 2) return terms == 2 ? launch_tc<true, 2>(a, st) : launch_tc<true, 1>(a, st);
     return terms == 2 ? launch_tc<false, 2>(a, st) : launch_tc<false, 1>(a, st);
 }
 
@@ -915,7 +933,9 @@ cudaError_t launch_quantize(const SegTable &segs, int64_t n, int32_t dim, int pr
     int64_t g = (n * 32 + 255) / 256;
     if (g > 16384) g = 16384;
     if (g < 1) g = 1;
-    if (prec == 2)
+    if (prec == 2 && q_lo)
+        quantize_kernel<true, true><<<(unsigned)g, 256, 0, st>>>(segs, n, dim, q, q_lo, scale, err, norm);
+    else if (prec == 2)
         quantize_kernel<true, false><<<(unsigned)g, 256, 0, st>>>(segs, n, dim, q, nullptr, scale, err, norm);
     else if (q_lo)
         quantize_kernel<false, true><<<(unsigned)g, 256, 0, st>>>(segs, n, dim, q, q_lo, scale, err, norm);
