@@ -875,6 +875,29 @@ def measure_extra(W, rn, torch, steps, warm, nq, scale=1.0, curves=False):
         r["recall_at_10"]["rnsm_segment_entries"] = curve(
             out, [int(graphs[k][1] + offs[k]) for k in range(len(sizes))])
         del gr
+        # denser merge plans on the same inputs: Algorithm 3 with a larger degree
+        # bound, and every pair once (the edges of the complete merge graph in the
+        # plan's execution order: closer pairs first, smaller into larger)
+        m = len(sizes)
+        cost = {(a, b): float(np.linalg.norm(cen[a].astype(np.float64) - cen[b]))
+                for a in range(m) for b in range(a + 1, m)}
+        allp = sorted(cost, key=lambda e: (cost[e], e))
+        allp = [((b, a) if sizes[b] < sizes[a] or (sizes[a] == sizes[b]) else (a, b)) + (cost[(a, b)],)
+                for a, b in allp]
+        for name, plan in (("rnsm_mos_degree6", rn.mos_plan(sizes, cen, degree_bound=6)),
+                           ("rnsm_all_pairs", allp)):
+            op = torch.empty_like(out)
+            pp = rn.params(W.R, W.L, W.alpha, metric=W.metric)
+            rn.merge(tsegs, pp, plan=plan, out=op)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rn.merge(tsegs, pp, plan=plan, out=op)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            r[name] = {"plan_edges": len(plan), "ms_per_step": e0.elapsed_time(e1)}
+            r["recall_at_10"][name] = curve(op, entry)
+            del op
     del out, tsegs, graphs, vd, Xd
     return r
 

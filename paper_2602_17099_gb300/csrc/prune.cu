@@ -103,6 +103,25 @@ __device__ __forceinline__ void stage_rows(float4 *rows, const float *const *rpt
     }
 }
 
+// The same staging by cp.async: every row's copies are in flight at once and
+// the caller waits once (cp_async_wait_all, then a barrier).
+template <int NT>
+__device__ __forceinline__ void stage_rows_async(float4 *rows, const float *const *rptr, int nrows4,
+                                                 int d0, int dc4) {
+    constexpr int NW = NT / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int f = lane; f - lane < dc4; f += 32) {
+        if (f >= dc4) continue;
+        for (int r = warp; r < nrows4; r += NW)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(static_cast<uint32_t>(
+                             __cvta_generic_to_shared(&rows[srow4(r) + f]))),
+                         "l"(rptr[r] + d0 + 4 * f)
+                         : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 __device__ __forceinline__ void stage(const Smem &s, int nrows4, int d0, int dc4) {
     stage_rows<kThreads>(s.rows, s.rptr, nrows4, d0, dc4);
 }
@@ -573,7 +592,8 @@ __global__ void __launch_bounds__(kSmallThreads, RNSM_SMALL_MIN_BLOCKS) prune_sm
                 for (int q = 0; q < 4; ++q) acc[t][p][q] = 0ull;
         for (int d0 = 0; d0 < dim; d0 += kDch) {
             const int dc4 = min(kDch, dim - d0) >> 2;
-            stage_rows<kSmallThreads, RNSM_SMALL_STAGE_UNROLL>(s.rows, s.rptr, 4 * nB, d0, dc4);
+            stage_rows_async<kSmallThreads>(s.rows, s.rptr, 4 * nB, d0, dc4);
+            cp_async_wait_all();
             __syncthreads();
 #pragma unroll
             for (int t = 0; t < kSmallNB; ++t) {

@@ -398,17 +398,19 @@ __global__ void __launch_bounds__(kQT, 4) prune_pair_kernel(const PruneArgs a, i
                 // split into hi + lo, is the staged row (centred on the owner)
                 f2_t acc = 0ull;
                 const float *v = s.vrow[o];
-                for (int u0 = 0; u0 < U; u0 += 4) {
-                    float4 xa[4][2];
+                // kRowBatch 16-byte units of the row in flight at a time
+                constexpr int kRowBatch = 4;
+                for (int u0 = 0; u0 < U; u0 += kRowBatch) {
+                    float4 xa[kRowBatch][2];
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
+                    for (int k = 0; k < kRowBatch; ++k) {
                         if (u0 + k < U) {
                             xa[k][0] = ldg4(xrow + 8 * (u0 + k));
                             xa[k][1] = ldg4(xrow + 8 * (u0 + k) + 4);
                         }
                     }
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
+                    for (int k = 0; k < kRowBatch; ++k) {
                         const int u = u0 + k;
                         if (u >= U) break;
                         const float4 v0 = *reinterpret_cast<const float4 *>(v + 8 * u);
