@@ -45,6 +45,7 @@ PRUNE_SRC = [os.path.join(ROOT, "paper_2602_17099_gb300", "csrc", f)
              for f in ("prune.cu", "common.cuh")]
 PRUNE_PROFILE = os.path.join(ROOT, "profiles", "prune_small_kernel_sift2x500k.txt")
 L2_PROFILE = os.path.join(ROOT, "profiles", "search_kernel_s5_sift2x200k.md")
+PRUNE_FULL_PROFILE = os.path.join(ROOT, "profiles", "prune_small_kernel_sift2x200k.md")
 L2_METRIC, IP_METRIC = 0, 1
 
 
@@ -372,6 +373,13 @@ def prune_profile_traffic():
                            "dram bytes per S6 launch")
 
 
+def prune_profile_fma():
+    """FMA-pipe activity (percent of peak) of the FP32 small-pool prune, from the
+    committed small-case ncu capture of the current sources."""
+    return profile_traffic(PRUNE_FULL_PROFILE, PRUNE_SRC, "prune sources sha256[:16]",
+                           "fma pipe active pct (S6)")
+
+
 def search_profile_l2():
     """L2 throughput of the search kernel (percent of its peak) and its L2 hit
     rate, from the committed small-case ncu capture of the current sources."""
@@ -521,7 +529,8 @@ def run_ours(args, ws, rank, local):
         # MOS runs inside the timed step (a host planner over sizes and centroids)
         return rn.mos_plan(sizes, cen) if W.multi else None
 
-    p = rn.params(W.R, W.L, W.alpha, metric=W.metric)
+    prec0 = {"fp32": rn.FP32, "bf16": rn.BF16, "fp8": rn.FP8}[args.precision]
+    p = rn.params(W.R, W.L, W.alpha, metric=W.metric, prec=prec0)
     out = torch.empty((N, W.R), dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
 
@@ -613,7 +622,9 @@ def run_ours(args, ws, rank, local):
                   "peak": alu_peak, "unit": "TFLOP/s", "frac_at_most": f_ach / alu_peak,
                   "peak_source": "derived: %d SMs x 128 FP32 lanes x 2 FLOP x %.0f MHz" % (
                       sm_count, float(peaks.get("sm_max_mhz", 2070.0))),
-                  "flop_per_owner_at_most": W.R * pool * W.dim * 2}
+                  "flop_per_owner_at_most": W.R * pool * W.dim * 2,
+                  # measured: the FMA pipe's activity in the committed ncu capture
+                  "fma_pipe_active_pct_ncu": prune_profile_fma() if W.name == "sift2x500k" else None}
     # the dominant kernel family of the FP32 step by live time goes first
     s7_ms = sum(st["phase_ms"][7] for st in stats)
     if p_ms + s7_ms >= s_ms:
@@ -674,7 +685,8 @@ def run_ours(args, ws, rank, local):
         qms = q0.elapsed_time(q1) / nq
         modes["fp32_cuda_graph"] = {"ms_per_step": qms, "value": N / (qms / 1000.0), "unit": UNIT,
                                     "identical_to_fp32": bool(torch.equal(og, ref_out))}
-    modes["fp32"] = {"ms_per_step": ms_max / args.steps,
+    modes["fp32" if args.precision == "fp32" else args.precision + "_timed_steps"] = {
+                     "ms_per_step": ms_max / args.steps,
                      "prune_ms": round(phase_ms["S6_source_prune"] + phase_ms["S7_reverse_edges"], 3)}
 
     progress("precision modes done")
@@ -740,7 +752,7 @@ def run_ours(args, ws, rank, local):
                 "config": {"workload": W.desc, "segments": sizes,
                            "dim": W.dim, "R": W.R, "L": W.L, "alpha": W.alpha,
                            "metric": "l2" if W.metric == L2_METRIC else "ip",
-                           "precision": "fp32",
+                           "precision": args.precision,
                            "plan": None if plan_used is None else [list(e[:2]) for e in plan_used],
                            "parallelism": "replicas" if ws > 1 else "single",
                            "l2": f"inputs larger than L2 ({vec_bytes >> 20} MB of vectors)",
@@ -1020,6 +1032,9 @@ def main():
     ap.add_argument("--n-per-seg", type=int, default=0,
                     help="sift2x500k only: rows per segment (overrides --scale)")
     ap.add_argument("--recall-queries", type=int, default=1000)
+    ap.add_argument("--precision", choices=["fp32", "bf16", "fp8"], default="fp32",
+                    help="prune tiles of the timed steps (the headline is FP32; the other "
+                         "modes are measured beside it either way)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the multi-segment workloads the default run also measures")

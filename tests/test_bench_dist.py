@@ -73,3 +73,15 @@ def test_profile_traffic_only_for_matching_sources(tmp_path):
     assert bench.profile_traffic(str(prof), [str(src)], "sources sha256[:16]",
                                  "bytes per launch") is None
     assert bench.profile_traffic(str(tmp_path / "none.txt"), [str(src)], "a", "b") is None
+
+
+def test_committed_profiles_match_the_current_sources():
+    # the bench reads DRAM traffic, L2 and FMA-pipe figures from the committed ncu
+    # summaries only while they were taken on the current kernel sources
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.prune_profile_traffic() is not None
+    assert bench.search_profile_traffic() is not None
+    assert bench.prune_profile_fma() is not None
+    l2 = bench.search_profile_l2()
+    assert l2 and 0 < l2["l2_hit_rate_pct"] <= 100 and 0 < l2["l2_throughput_pct"] <= 100
