@@ -995,9 +995,37 @@ def run_incremental(args, ws, rank, local):
         modes[name] = {"ms_per_step": qms, "value": units / (qms / 1000.0), "unit": UNIT,
                        "identical_to_fp32": bool(torch.equal(fq, ref)),
                        "rechecks_per_step": int(sum(st["rechecks"] for st in sq))}
+    # the multi-pair union variant: the partitions merged three at a time (each
+    # into the index, the later ones also into the earlier ones), one prune per
+    # source vertex and one reverse-edge pass per step
+    def sequence_union(p, group=3):
+        g, e = graphs[0]
+        n_idx, nstep = n_part, 0
+        for k0 in range(1, m, group):
+            ks = list(range(k0, min(m, k0 + group)))
+            plan = [(i + 1, 0, 0.0) for i in range(len(ks))]
+            plan += [(j + 1, i + 1, 0.0) for i in range(len(ks)) for j in range(i + 1, len(ks))]
+            out = bufs[nstep % 2][:n_idx + len(ks) * n_part]
+            g, _ = rn.merge([(allx[:n_idx], g, e)] + [(segs[k], graphs[k][0], graphs[k][1]) for k in ks],
+                            p, plan=plan, out=out)
+            n_idx += len(ks) * n_part
+            nstep += 1
+        return g
+    pu = rn.params(W.R, W.L, W.alpha, metric=W.metric, flags=rn.FLAG_UNION)
+    sequence_union(pu)
+    torch.cuda.synchronize()
+    q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    q0.record(stream)
+    fu = sequence_union(pu)
+    q1.record(stream)
+    torch.cuda.synchronize()
+    union = {"ms_per_sequence": q0.elapsed_time(q1), "merges": (m - 1 + 2) // 3,
+             "note": "three partitions per merge call (RNSM_FLAG_UNION); sequential: nine calls"}
     rec = None
     if args.recall_queries > 0:
         rec = recall_at_10(rn, torch, W, allx, ref, entry, Q[:args.recall_queries])
+        union["recall_at_10"] = recall_at_10(rn, torch, W, allx, fu, entry, Q[:args.recall_queries])
+    modes["union3"] = union
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,

@@ -508,3 +508,28 @@ def test_expand_autotuned_on_large_batch(rn):
     want, _, _, _ = oracle.expand(X, adj, 12)
     got = rn.expand(dev(X), dev(adj), 12)
     np.testing.assert_array_equal(host(got), want)
+
+
+@pytest.mark.parametrize("kind", ["sift", "deepl2"])
+def test_prune_variants_and_autotuned_choice_agree(rn, monkeypatch, kind):
+    # the prune variants (pair tile, general tile, FP32 kernels) take the FP32
+    # decisions; 70,000 owners trigger the autotuner (slices of the owners run
+    # with each variant in turn), whose choice must not change the result
+    n = 80000
+    X = gen.sift_like(n, 111, d=128) if kind == "sift" else gen.deep_like(n, 112, d=96)
+    owners, pool = _pools(n, 64, 113, 70000)
+    Xd, od, pd_ = dev(X), dev(owners), dev(pool)
+    ref = host(rn.prune(Xd, od, pd_, 32, 1.2))
+    want, _ = oracle.prune(X, owners[:2000].astype(np.int64), pool[:2000], 32, 1.2)
+    if kind == "sift":   # integer rows: exact against the oracle
+        np.testing.assert_array_equal(ref[:2000], want)
+    for prec in (rn.BF16, rn.FP8):
+        for force in ("1", "2", "0", None):
+            if force is None:
+                monkeypatch.delenv("RNSM_PRUNE_VARIANT", raising=False)
+            else:
+                monkeypatch.setenv("RNSM_PRUNE_VARIANT", force)
+            got = host(rn.prune(Xd, od, pd_, 32, 1.2, prec=prec))
+            np.testing.assert_array_equal(got, ref, err_msg=f"prec {prec} variant {force}")
+        # the tuned choice, reused
+        np.testing.assert_array_equal(host(rn.prune(Xd, od, pd_, 32, 1.2, prec=prec)), ref)
