@@ -660,6 +660,9 @@ def run_ours(args, ws, rank, local):
         modes[name] = {"ms_per_step": qms, "value": N / (qms / 1000.0), "unit": UNIT,
                        "identical_to_fp32": bool(torch.equal(oq, ref_out)),
                        "rechecks_per_step": qs[-1]["rechecks"],
+                       "tile_tests_per_step": qs[-1]["tile_tests"],
+                       "rechecked_share": (qs[-1]["rechecks"] / qs[-1]["tile_tests"]
+                                           if qs[-1]["tile_tests"] else None),
                        # sampled owner distances: tile and FP32 vs FP64, bound use
                        "distance_error": {
                            "tile_vs_fp64_max_rel": qs[-1]["tile_error"][0],
@@ -846,6 +849,8 @@ def measure_extra(W, rn, torch, steps, warm, nq, scale=1.0, curves=False):
         r[name] = {"ms_per_step": msq, "value": N / (msq / 1000.0), "unit": UNIT,
                    "identical_to_fp32": bool(torch.equal(oq, out)),
                    "rechecks_per_step": int(stq["rechecks"]),
+                   "tile_tests_per_step": int(stq["tile_tests"]),
+                   "rechecked_share": (stq["rechecks"] / stq["tile_tests"] if stq["tile_tests"] else None),
                    "tile_vs_fp32_max_share_of_bound": stq["tile_error"][2],
                    "prune_ms": round(stq["phase_ms"][6] + stq["phase_ms"][7], 3)}
     del oq

@@ -151,6 +151,10 @@ typedef struct {
      * [2] max |d~ - d32| / B (the share of its error bound B the tile used),
      * [3] number of distances sampled.  Zero in FP32 mode. */
     double tile_error[4];
+    /* BF16 / FP8 modes: occlusion tests the tensor-core tiles evaluated (the
+     * share that was re-decided is rechecks / tile_tests, owner-distance
+     * re-decisions of the general tile included in rechecks).  Zero in FP32. */
+    int64_t tile_tests;
 } rnsm_stats;
 
 /*

@@ -122,6 +122,7 @@ struct Ctl {
     unsigned long long *stats;  // per search slot s: [2s] ndc, [2s+1] expansions
     unsigned long long *ecount;
     unsigned long long *rechecks;  // prune decisions re-decided in FP32
+    unsigned long long *tile_tests;  // occlusion tests evaluated by the tensor-core tiles
     unsigned int *tile_err;  // [4] tile error statistics (see rnsm_stats)
     int32_t *scratch_i;      // misc int
 };
@@ -152,8 +153,9 @@ void take_quant(Bump &b, int64_t n, int32_t dim, int32_t prec, int32_t metric, Q
 }
 
 void apply_quant(PruneArgs &a, const QuantBufs *qb, unsigned long long *rechecks,
-                 unsigned int *tile_err = nullptr) {
+                 unsigned int *tile_err = nullptr, unsigned long long *tile_tests = nullptr) {
     a.rechecks = rechecks;
+    a.tile_tests = tile_tests;
     if (!qb || qb->prec == 0) return;
     a.tile_err = tile_err;
     a.prec = qb->prec;
@@ -185,6 +187,7 @@ void take_ctl(Bump &b, Ctl &c, int64_t max_owners = 0) {
     c.stats = b.take<unsigned long long>(8);
     c.ecount = b.take<unsigned long long>(1);
     c.rechecks = b.take<unsigned long long>(1);
+    c.tile_tests = b.take<unsigned long long>(1);
     c.tile_err = b.take<unsigned int>(4);
     c.scratch_i = b.take<int32_t>(4);
 }
@@ -193,6 +196,7 @@ rnsm_status ctl_reset(const Ctl &c, cudaStream_t st) {
     CK(cudaMemsetAsync(c.err, 0, sizeof(int32_t), st));
     CK(cudaMemsetAsync(c.stats, 0, 8 * sizeof(unsigned long long), st));
     CK(cudaMemsetAsync(c.rechecks, 0, sizeof(unsigned long long), st));
+    CK(cudaMemsetAsync(c.tile_tests, 0, sizeof(unsigned long long), st));
     CK(cudaMemsetAsync(c.tile_err, 0, 4 * sizeof(unsigned int), st));
     return RNSM_OK;
 }
@@ -351,7 +355,7 @@ rnsm_status reverse_into(const SegTable &tab, int32_t dim, const rnsm_params &p,
     a.csr_max = csr_max;
     a.out = lists;
     a.err = c.err;
-    apply_quant(a, qb, c.rechecks, c.tile_err);
+    apply_quant(a, qb, c.rechecks, c.tile_err, c.tile_tests);
     return run_prune(a, c.work + 6, c, st);
 }
 
@@ -618,7 +622,7 @@ rnsm_status rnsm_prune(const float *vecs, int64_t n, int32_t dim, const int32_t 
     a.err = c.err;
     if (qb.q) CK(launch_quantize(tab, n, dim, qprec, qb.q, qb.qlo, qb.scale, qb.err, qb.norm, st));
     TRY(pair_exactness(tab, dim, qprec, metric, c, st, qb));
-    apply_quant(a, &qb, c.rechecks);
+    apply_quant(a, &qb, c.rechecks, nullptr, c.tile_tests);
     TRY(run_prune(a, c.work + 8, c, st));
     TRY(check_err_word(c, st));
     return RNSM_OK;
@@ -1290,7 +1294,7 @@ rnsm_status rnsm_merge(const rnsm_segment *segs, int32_t m, const rnsm_params *p
                 q.offB = 0;
                 q.out = out_adj;
                 q.err = c.err;
-                apply_quant(q, &mb.qb, c.rechecks, c.tile_err);
+                apply_quant(q, &mb.qb, c.rechecks, c.tile_err, c.tile_tests);
                 TRY(run_prune(q, c.work + 8, c, es));
             }
             tm.end(span);
@@ -1332,7 +1336,7 @@ rnsm_status rnsm_merge(const rnsm_segment *segs, int32_t m, const rnsm_params *p
             q.ev = mb.ev;
             q.ecount = c.ecount;
             q.err = c.err;
-            apply_quant(q, &mb.qb, c.rechecks, c.tile_err);
+            apply_quant(q, &mb.qb, c.rechecks, c.tile_err, c.tile_tests);
             TRY(run_prune(q, c.work + 8, c, es));
             tm.end(span);
             span = graph ? -1 : tm.begin(7);
@@ -1410,6 +1414,8 @@ rnsm_status rnsm_merge(const rnsm_segment *segs, int32_t m, const rnsm_params *p
         unsigned long long rc = 0;
         unsigned int te[4] = {0, 0, 0, 0};
         CK(cudaMemcpyAsync(&rc, c.rechecks, sizeof(rc), cudaMemcpyDeviceToHost, st));
+        unsigned long long tt = 0;
+        CK(cudaMemcpyAsync(&tt, c.tile_tests, sizeof(tt), cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(te, c.tile_err, sizeof(te), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         for (int i = 0; i < 3; ++i) {
@@ -1427,6 +1433,7 @@ rnsm_status rnsm_merge(const rnsm_segment *segs, int32_t m, const rnsm_params *p
         }
         stats->launches = launches_so_far() - launches0;
         stats->rechecks = (int64_t)rc;
+        stats->tile_tests = (int64_t)tt;
         stats->pivots = n_piv;
         stats->followers = n_fol;
         stats->reverse_edges = (int64_t)rev_total;

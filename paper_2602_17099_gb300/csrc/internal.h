@@ -115,6 +115,7 @@ struct PruneArgs {
     const float *qerr;        // residual norms ||x - x~||
     const float *qnorm;       // row norms ||x||
     unsigned long long *rechecks;  // decisions re-decided in FP32
+    unsigned long long *tile_tests;  // nullable: occlusion tests the tensor-core tiles evaluated
     unsigned int *tile_err;   // nullable [4]: sampled tile error maxima (float bits) and count
     int32_t *work;
     int32_t *work2;           // second zeroed counter (overflow pass)
@@ -126,6 +127,13 @@ struct PruneArgs {
 };
 
 cudaError_t launch_prune(const PruneArgs &a, cudaStream_t st);
+// The FP32 kernels behind it: the small-pool kernel (raw pools of at most
+// kPruneSmallMax; larger ones go to a->ovf_list) and the general kernel (with
+// idx_list: only the listed owner indices, idx_count of them on the device).
+constexpr int kPruneSmallMax = 64;
+cudaError_t launch_small(const PruneArgs &a, cudaStream_t st);
+cudaError_t launch_prune_general(const PruneArgs &a, const int32_t *idx_list,
+                                 const unsigned long long *idx_count, cudaStream_t st);
 
 // Tensor-core prune (BF16 / FP8 tiles with FP32 re-decisions) of pools up to
 // prune_tc_max_pool() raw candidates.  prune_tc_terms: 0 if (dim, prec) has no

@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(kQT, 4) prune_pair_kernel(const PruneArgs a, i
     const uint32_t taddr = s.tmem_slot;
     const uint32_t tbase = tc::smem_u32(tile);
     uint32_t phase = 0;
-    unsigned long long rechecks = 0;
+    unsigned long long rechecks = 0, tests = 0;
 
     for (;;) {
         if (tid == 0) sh_i = atomicAdd(a.work, chunk);
@@ -580,6 +580,8 @@ __global__ void __launch_bounds__(kQT, 4) prune_pair_kernel(const PruneArgs a, i
                     uint32_t rv[16];
                     tc::tmem_ld16(tl + 64 * o + c0, rv);
                     tc::tmem_wait_ld();
+                    tests += (unsigned long long)__popc(a16);
+                    uint32_t obits = 0;   // this lane's open tests of the chunk
 #pragma unroll
                     for (int q = 0; q < 16; ++q) {
                         const int c = c0 + q;
@@ -589,23 +591,41 @@ __global__ void __launch_bounds__(kQT, 4) prune_pair_kernel(const PruneArgs a, i
                         const bool act = (a16 >> q) & 1u;
                         const float up = fmaf(m2a, g, pqc.x + As);
                         const float dn = fmaf(m2a, g, pqc.y + As2);
-                        bool occl = act && up < 0.f;
-                        const bool open = act && !(up < 0.f) && !(dn > 0.f);
-                        const unsigned om = __ballot_sync(0xffffffffu, open);
-                        if (open) {
-                            const int k = nq + __popc(om & lanemask_lt());
+                        obits |= act && !(up < 0.f) && !(dn > 0.f) ? 1u << q : 0u;
+                        const unsigned m = __ballot_sync(0xffffffffu, act && up < 0.f);
+                        if (lane == 0) s.occ[o][c][h] = m;
+                    }
+                    if (__any_sync(0xffffffffu, obits != 0u)) {
+                        __syncwarp();   // the occluder words above are written
+                        // (the chunk's tile values again: cheaper than keeping them live)
+                        tc::tmem_ld16(tl + 64 * o + c0, rv);
+                        tc::tmem_wait_ld();
+                        // queue slots: an exclusive prefix of the lanes' open counts
+                        const int cnt = __popc(obits);
+                        int pre = cnt;
+#pragma unroll
+                        for (int d = 1; d < 32; d <<= 1) {
+                            const int t = __shfl_up_sync(0xffffffffu, pre, d);
+                            if (lane >= d) pre += t;
+                        }
+                        int k = nq + pre - cnt;
+                        nq += __shfl_sync(0xffffffffu, pre, 31);
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) {
+                            if (!((obits >> q) & 1u)) continue;
+                            const int c = c0 + q;
+                            float g = __uint_as_float(rv[q]);
+                            if (kF8) g *= isc_t * s.isc[o][c];
                             if (k < kQOpen) {
                                 s.open_q[warp][k] = make_uint2(__float_as_uint(g), (uint32_t)c | ((uint32_t)p << 8));
-                            } else {
+                            } else {   // queue full: decided here
                                 const int res = decide_open(g, gs, ns2, s.gd[o][c], s.nn[o][c], s.sd[o][c],
                                                             xrow, s.rp[o][c], dim, alpha, e1, kE, gam);
-                                occl = res & 1;
                                 rechecks += (unsigned long long)(res >> 1);
+                                if (res & 1) atomicOr(&s.occ[o][c][h], 1u << lane);
                             }
+                            ++k;
                         }
-                        nq += __popc(om);
-                        const unsigned m = __ballot_sync(0xffffffffu, occl);
-                        if (lane == 0) s.occ[o][c][h] = m;
                     }
                 }
                 __syncwarp();
@@ -734,6 +754,7 @@ __global__ void __launch_bounds__(kQT, 4) prune_pair_kernel(const PruneArgs a, i
         if (sh_fail) break;
     }
     if (rechecks && a.rechecks) atomicAdd(a.rechecks, rechecks);
+    if (tests && a.tile_tests) atomicAdd(a.tile_tests, tests);
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(taddr, kQCols);

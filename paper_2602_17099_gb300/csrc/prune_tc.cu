@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(kThreads, 2) prune_tc_kernel(const PruneArgs a
     // and occ[c] (bit s set if kept s would drop c)
     uint32_t *const undecided = reinterpret_cast<uint32_t *>(raw0);
     uint32_t (*const occ)[4] = reinterpret_cast<uint32_t (*)[4]>(raw0 + kRawBytes);
-    unsigned long long rechecks = 0;
+    unsigned long long rechecks = 0, tests = 0;
     // IP rows whose tile terms the library stored (the quantized copies, or hi and lo
     // for two terms) go straight from global memory into the tile: no conversion
     const bool direct = metric != 0 && (kTerms == 1 || a.qrows_lo != nullptr);
@@ -619,6 +619,7 @@ __global__ void __launch_bounds__(kThreads, 2) prune_tc_kernel(const PruneArgs a
                     const int c = 16 * ch + q;
                     bool occl = false;
                     if (c < nc && s_ok && s.live[c] && s_rank < s.rank[c]) {
+                        ++tests;
                         const float g = __uint_as_float(r16[q]) * scs * s.sc[c];
                         const float Ec = s.E[c];
                         const float E = Es + Ec;
@@ -797,6 +798,7 @@ __global__ void __launch_bounds__(kThreads, 2) prune_tc_kernel(const PruneArgs a
         if (sh_fail) break;
     }
     if (rechecks && a.rechecks) atomicAdd(a.rechecks, rechecks);
+    if (tests && a.tile_tests) atomicAdd(a.tile_tests, tests);
     if (sh_fail) {  // give MMAs that did not finish a second bounded chance before freeing TMEM
         if (pend0) tc::mbar_wait_bounded(&s.bar[0], ph0, kWaitNs);
         if (pend1) tc::mbar_wait_bounded(&s.bar[1], ph1, kWaitNs);

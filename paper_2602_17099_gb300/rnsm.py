@@ -56,7 +56,8 @@ class Stats(C.Structure):
                 ("followers", C.c_int64), ("reverse_edges", C.c_int64),
                 ("launches", C.c_int64), ("phase_ms", C.c_double * 8),
                 ("search_ndc", C.c_int64 * 3), ("search_exp", C.c_int64 * 3),
-                ("search_queries", C.c_int64 * 3), ("tile_error", C.c_double * 4)]
+                ("search_queries", C.c_int64 * 3), ("tile_error", C.c_double * 4),
+                ("tile_tests", C.c_int64)]
 
     def as_dict(self):
         out = {}
