@@ -43,9 +43,15 @@ SEARCH_SRC = [os.path.join(ROOT, "paper_2602_17099_gb300", "csrc", f)
 PROFILE = os.path.join(ROOT, "profiles", "search_kernel_sift2x500k.txt")
 PRUNE_SRC = [os.path.join(ROOT, "paper_2602_17099_gb300", "csrc", f)
              for f in ("prune.cu", "common.cuh")]
-PRUNE_PROFILE = os.path.join(ROOT, "profiles", "prune_small_kernel_sift2x500k.txt")
 L2_PROFILE = os.path.join(ROOT, "profiles", "search_kernel_s5_sift2x200k.md")
-PRUNE_FULL_PROFILE = os.path.join(ROOT, "profiles", "prune_small_kernel_sift2x200k.md")
+# the FP32 prune kernels of pools <= 64, by the variant number the library
+# reports (stats prune_kernel): their kernel name and committed ncu summaries
+# (full-size DRAM traffic, small-case FMA-pipe activity)
+PRUNE_KERNELS = {
+    0: ("prune_small_kernel", "prune_small_kernel_sift2x500k.txt", "prune_small_kernel_sift2x200k.md"),
+    3: ("prune_walk_kernel", "prune_walk_kernel_sift2x500k.txt", "prune_walk_kernel_sift2x200k.md"),
+}
+PRUNE_DEFAULT_VARIANT = 3
 L2_METRIC, IP_METRIC = 0, 1
 
 
@@ -368,16 +374,23 @@ def search_profile_traffic():
                            "dram bytes per launch (mean of S1, S4, S5)")
 
 
-def prune_profile_traffic():
-    return profile_traffic(PRUNE_PROFILE, PRUNE_SRC, "prune sources sha256[:16]",
-                           "dram bytes per S6 launch")
+def _prune_profile(variant, k):
+    v = PRUNE_KERNELS.get(variant)
+    return os.path.join(ROOT, "profiles", v[k]) if v else None
 
 
-def prune_profile_fma():
-    """FMA-pipe activity (percent of peak) of the FP32 small-pool prune, from the
-    committed small-case ncu capture of the current sources."""
-    return profile_traffic(PRUNE_FULL_PROFILE, PRUNE_SRC, "prune sources sha256[:16]",
-                           "fma pipe active pct (S6)")
+def prune_profile_traffic(variant=PRUNE_DEFAULT_VARIANT):
+    path = _prune_profile(variant, 1)
+    return path and profile_traffic(path, PRUNE_SRC, "prune sources sha256[:16]",
+                                    "dram bytes per S6 launch")
+
+
+def prune_profile_fma(variant=PRUNE_DEFAULT_VARIANT):
+    """FMA-pipe activity (percent of peak) of an FP32 small-pool prune kernel,
+    from the committed small-case ncu capture of the current sources."""
+    path = _prune_profile(variant, 2)
+    return path and profile_traffic(path, PRUNE_SRC, "prune sources sha256[:16]",
+                                    "fma pipe active pct (S6)")
 
 
 def search_profile_l2():
@@ -604,11 +617,14 @@ def run_ours(args, ws, rank, local):
     p_ms = sum(st["phase_ms"][6] for st in stats)
     n_p6 = len(stats) * (len(plan_used) if plan_used else 1)
     p_ach = owners * b_per_owner / (p_ms / 1000.0) / 1e9
+    s6_var = stats[-1]["prune_kernel"][0]
+    s6_name = (PRUNE_KERNELS[s6_var][0] if pool <= 64 and s6_var in PRUNE_KERNELS
+               else "prune_kernel")
     prune_roof = {"bound": "hbm",
-                  "kernel": ("prune_small_kernel" if pool <= 64 else "prune_kernel") + " (S6 launches)",
+                  "kernel": s6_name + " (S6 launches)",
                   "achieved": p_ach, "peak": peak, "unit": "GB/s", "frac": p_ach / peak,
                   "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
-                  "traffic": prune_profile_traffic() if full_default else None,
+                  "traffic": prune_profile_traffic(s6_var) if full_default else None,
                   "algorithmic_bytes_per_launch": owners * b_per_owner / n_p6,
                   "algorithmic_bytes_per_owner": b_per_owner,
                   "avg_launch_ms": p_ms / n_p6}
@@ -624,7 +640,7 @@ def run_ours(args, ws, rank, local):
                       sm_count, float(peaks.get("sm_max_mhz", 2070.0))),
                   "flop_per_owner_at_most": W.R * pool * W.dim * 2,
                   # measured: the FMA pipe's activity in the committed ncu capture
-                  "fma_pipe_active_pct_ncu": prune_profile_fma() if W.name == "sift2x500k" else None}
+                  "fma_pipe_active_pct_ncu": prune_profile_fma(s6_var) if W.name == "sift2x500k" else None}
     # the dominant kernel family of the FP32 step by live time goes first
     s7_ms = sum(st["phase_ms"][7] for st in stats)
     if p_ms + s7_ms >= s_ms:

@@ -155,6 +155,11 @@ typedef struct {
      * share that was re-decided is rechecks / tile_tests, owner-distance
      * re-decisions of the general tile included in rechecks).  Zero in FP32. */
     int64_t tile_tests;
+    /* The prune kernel that served the last S6 call and the last S7 pool prune
+     * (the autotuner's choice): 0 the FP32 register-blocked triangle, 1 the
+     * pair tensor-core tile, 2 the general tensor-core tile, 3 the FP32 walk
+     * over kept rows; -1 none ran. */
+    int32_t prune_kernel[2];
 } rnsm_stats;
 
 /*

@@ -125,6 +125,7 @@ struct Ctl {
     unsigned long long *tile_tests;  // occlusion tests evaluated by the tensor-core tiles
     unsigned int *tile_err;  // [4] tile error statistics (see rnsm_stats)
     int32_t *scratch_i;      // misc int
+    int32_t *kernel_ran = nullptr;  // host [2]: prune variant of the last S6 / S7 call
 };
 
 // Quantized copies of the rows for the tensor-core prune (prec 1 or 2).
@@ -296,13 +297,16 @@ PruneArgs prune_defaults() {
     return a;
 }
 
-rnsm_status run_prune(PruneArgs a, int32_t *work, const Ctl &c, cudaStream_t st) {
+// slot: 0 an S6 call, 1 an S7 call (recorded in c.kernel_ran), -1 neither
+rnsm_status run_prune(PruneArgs a, int32_t *work, const Ctl &c, cudaStream_t st, int slot = -1) {
     CK(cudaMemsetAsync(work, 0, 2 * sizeof(int32_t), st));
     a.work = work;
     a.work2 = work + 1;
     a.ovf_list = c.ovf;
     a.ovf_count = c.ovf_count;
-    CK(launch_prune(a, st));
+    int ran = -1;
+    CK(launch_prune(a, st, &ran));
+    if (slot >= 0 && c.kernel_ran) c.kernel_ran[slot] = ran;
     return RNSM_OK;
 }
 
@@ -356,7 +360,7 @@ rnsm_status reverse_into(const SegTable &tab, int32_t dim, const rnsm_params &p,
     a.out = lists;
     a.err = c.err;
     apply_quant(a, qb, c.rechecks, c.tile_err, c.tile_tests);
-    return run_prune(a, c.work + 6, c, st);
+    return run_prune(a, c.work + 6, c, st, 1);
 }
 
 }  // namespace
@@ -1055,6 +1059,8 @@ rnsm_status rnsm_merge(const rnsm_segment *segs, int32_t m, const rnsm_params *p
     carve_merge(b, p, nmax, off, res_rows, n_jobs, dim, qprec, c, mb, e_max);
     TRY(ws_acquire(b.off, b));
     carve_merge(b, p, nmax, off, res_rows, n_jobs, dim, qprec, c, mb, e_max);
+    int32_t kernel_ran[2] = {-1, -1};
+    c.kernel_ran = kernel_ran;
     TRY(ctl_reset(c, st));
     for (int32_t s = 0; s < m; ++s)
         TRY(validate_on_device(segs[s].vecs, segs[s].n, dim, segs[s].adj, segs[s].r_in, c, st));
@@ -1295,7 +1301,7 @@ rnsm_status rnsm_merge(const rnsm_segment *segs, int32_t m, const rnsm_params *p
                 q.out = out_adj;
                 q.err = c.err;
                 apply_quant(q, &mb.qb, c.rechecks, c.tile_err, c.tile_tests);
-                TRY(run_prune(q, c.work + 8, c, es));
+                TRY(run_prune(q, c.work + 8, c, es, 0));
             }
             tm.end(span);
             span = graph ? -1 : tm.begin(7);
@@ -1337,7 +1343,7 @@ rnsm_status rnsm_merge(const rnsm_segment *segs, int32_t m, const rnsm_params *p
             q.ecount = c.ecount;
             q.err = c.err;
             apply_quant(q, &mb.qb, c.rechecks, c.tile_err, c.tile_tests);
-            TRY(run_prune(q, c.work + 8, c, es));
+            TRY(run_prune(q, c.work + 8, c, es, 0));
             tm.end(span);
             span = graph ? -1 : tm.begin(7);
             TRY(reverse_into(tab, dim, p, out_adj, mb.eu, mb.ev, ns * p.R, c.ecount, t0, nt,
@@ -1434,6 +1440,8 @@ rnsm_status rnsm_merge(const rnsm_segment *segs, int32_t m, const rnsm_params *p
         stats->launches = launches_so_far() - launches0;
         stats->rechecks = (int64_t)rc;
         stats->tile_tests = (int64_t)tt;
+        stats->prune_kernel[0] = kernel_ran[0];
+        stats->prune_kernel[1] = kernel_ran[1];
         stats->pivots = n_piv;
         stats->followers = n_fol;
         stats->reverse_edges = (int64_t)rev_total;

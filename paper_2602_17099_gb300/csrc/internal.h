@@ -126,12 +126,17 @@ struct PruneArgs {
     int32_t pair_hi_only;     // pair tile: integer rows spanning <= 256, hi terms only
 };
 
-cudaError_t launch_prune(const PruneArgs &a, cudaStream_t st);
+// variant (optional): set to the prune variant that served the call (0 the
+// FP32 triangle, 1 the pair tile, 2 the general tile, 3 the FP32 walk).
+cudaError_t launch_prune(const PruneArgs &a, cudaStream_t st, int *variant = nullptr);
 // The FP32 kernels behind it: the small-pool kernel (raw pools of at most
 // kPruneSmallMax; larger ones go to a->ovf_list) and the general kernel (with
 // idx_list: only the listed owner indices, idx_count of them on the device).
 constexpr int kPruneSmallMax = 64;
 cudaError_t launch_small(const PruneArgs &a, cudaStream_t st);
+// The same pools (d <= kPruneWalkMaxDim) by the walk over kept rows only.
+constexpr int kPruneWalkMaxDim = 128;
+cudaError_t launch_walk(const PruneArgs &a, cudaStream_t st);
 cudaError_t launch_prune_general(const PruneArgs &a, const int32_t *idx_list,
                                  const unsigned long long *idx_count, cudaStream_t st);
 

@@ -796,6 +796,253 @@ __global__ void __launch_bounds__(kSmallThreads, RNSM_SMALL_MIN_BLOCKS) prune_sm
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// The greedy walk over kept rows only (pools of at most 64 raw candidates,
+// dim <= 128).  The walk needs d(s, c) only for a kept s before c: the
+// lowest open position (live, not yet occluded) is always kept, because
+// every kept position before it has been tested against it.  So the walk
+// goes kept row by kept row and tests each against the open positions after
+// it -- on SIFT-like source pools about 900 of the 2,080 pair distances of
+// the full triangle.  One CTA of 64 threads per owner; after ranking,
+// thread t holds the row of position t in registers and every row sits in
+// shared memory in position order, so the rows tested against are read as
+// broadcasts.  Each round takes the first kWalkB open positions at once
+// (kWalkB independent distance chains per thread): the first is kept, a
+// later one is kept iff none of the kept ones before it occludes it (their
+// mutual distances are among those computed), and the positions after the
+// batch drop what the kept ones occlude.  Distances by a dropped member of
+// the batch are discarded.  Every distance is the FP32 chain of the
+// triangle kernel (a pair's order does not change it), so the kept lists
+// are identical.
+constexpr int kWalkThreads = 64;
+constexpr int kWalkMaxF4 = 32;   // float4 of a row held in registers (dim <= 128)
+constexpr int kWalkStride = kWalkMaxF4 + 1;   // row stride in float4: 8 rows on 32 banks
+#ifndef RNSM_WALK_B
+#define RNSM_WALK_B 4
+#endif
+constexpr int kWalkB = RNSM_WALK_B;
+
+struct WalkSmem {
+    float4 rows[kSmallMax * kWalkStride];   // candidate rows in position order
+    float4 vrow[kWalkMaxF4];                // the owner's row
+    float kd[kSmallMax];                    // raw keys
+    int32_t kix[kSmallMax];
+    int32_t sid[kSmallMax];                 // ids in position order
+    float sd[kSmallMax];                    // d(v, c) in position order
+    uint32_t occ[2][kWalkB][2];             // a round's occluded positions, per warp
+    int64_t claim;
+};
+
+template <int kMetric>
+__global__ void __launch_bounds__(kWalkThreads, 5) prune_walk_kernel(const PruneArgs a, int chunk) {
+    __shared__ __align__(16) WalkSmem s;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int dim = a.dim, F4 = dim >> 2;
+    const int R = a.R;
+    for (;;) {
+        if (tid == 0) s.claim = atomicAdd(a.work, chunk);
+        __syncthreads();
+        const int64_t i0 = s.claim;
+        __syncthreads();   // every thread has read the claim
+        if (i0 >= a.n_owners) break;
+        const int64_t i1 = min(a.n_owners, i0 + chunk);
+        for (int64_t i = i0; i < i1; ++i) {
+            const int32_t owner = a.owner_ids ? a.owner_ids[i] : (int32_t)(a.owner_base + i);
+            int64_t c_lo = 0, c_hi = 0;
+            if (a.csr_offs) {
+                c_lo = a.csr_offs[i];
+                c_hi = a.csr_offs[i + 1];
+            }
+            if (a.skip_empty_csr && c_hi == c_lo) continue;   // uniform
+            const int64_t nr_raw = (int64_t)a.lenA + a.lenB + (c_hi - c_lo);
+            if (nr_raw > kSmallMax) {
+                if (tid == 0) a.ovf_list[atomicAdd(a.ovf_count, 1ull)] = (int32_t)i;
+                continue;
+            }
+            const int nr = (int)nr_raw;
+            // 1. raw candidate tid: its row into registers, the owner's row to
+            //    shared memory, the candidate's key (d(v,c), id)
+            int32_t id = -1;
+            if (tid < nr) {
+                if (tid < a.lenA) {
+                    id = a.listA[(int64_t)owner * a.lenA + tid];
+                } else if (tid < a.lenA + a.lenB) {
+                    id = a.listB[i * a.strideB + (tid - a.lenA)];
+                    if (id >= 0) id += a.offB;
+                } else {
+                    id = a.csr_ids[c_lo + (tid - a.lenA - a.lenB)];
+                }
+                if (id == owner) id = -1;
+            }
+            const float *orow = seg_row(a.segs, owner, dim);
+            if (tid < F4) s.vrow[tid] = ldg4(orow + 4 * tid);
+            float4 xr[kWalkMaxF4];
+            {
+                const float *row = seg_row(a.segs, id >= 0 ? id : owner, dim);
+#pragma unroll
+                for (int f = 0; f < kWalkMaxF4; ++f)
+                    if (f < F4) xr[f] = ldg4(row + 4 * f);
+            }
+            __syncthreads();
+            {
+                f2_t acc = 0ull;
+#pragma unroll
+                for (int f = 0; f < kWalkMaxF4; ++f)
+                    if (f < F4)
+                        acc = chain2(acc, *reinterpret_cast<const ulonglong2 *>(&s.vrow[f]),
+                                     *reinterpret_cast<const ulonglong2 *>(&xr[f]), kMetric);
+                const bool valid = tid < nr && id >= 0;
+                s.kd[tid] = valid ? chain2_final(acc, kMetric) : INFINITY;
+                s.kix[tid] = valid ? id : INT32_MAX;
+            }
+            __syncthreads();
+            // 2. position = rank by (d(v,c), id); duplicates (equal keys) rank by
+            //    raw index, so they land next to each other; -1 and the owner
+            //    last.  The row moves to its position's slot.
+            float my_dvc = 0.f;
+            if (tid < nr) {
+                const float dj = s.kd[tid];
+                const int32_t ij = s.kix[tid];
+                int r = 0;
+                for (int k = 0; k < nr; ++k) {
+                    const float dk = s.kd[k];
+                    const int32_t ik = s.kix[k];
+                    r += lex_less(dk, ik, dj, ij) || (dk == dj && ik == ij && k < tid);
+                }
+                s.sid[r] = ij;
+                s.sd[r] = dj;
+                float4 *dst = s.rows + r * kWalkStride;
+#pragma unroll
+                for (int f = 0; f < kWalkMaxF4; ++f)
+                    if (f < F4) dst[f] = xr[f];
+            }
+            __syncthreads();
+            if (tid < nr) {
+                const float4 *src = s.rows + tid * kWalkStride;
+#pragma unroll
+                for (int f = 0; f < kWalkMaxF4; ++f)
+                    if (f < F4) xr[f] = src[f];
+                my_dvc = s.sd[tid];
+            }
+            // live positions: valid and not a repeat of the previous id
+            unsigned long long live;
+            {
+                const bool a0 = lane < nr && s.sid[lane] != INT32_MAX &&
+                                (lane == 0 || s.sid[lane - 1] != s.sid[lane]);
+                const bool a1 = lane + 32 < nr && s.sid[lane + 32] != INT32_MAX &&
+                                s.sid[lane + 31] != s.sid[lane + 32];
+                live = (unsigned long long)__ballot_sync(0xffffffffu, a0) |
+                       ((unsigned long long)__ballot_sync(0xffffffffu, a1) << 32);
+            }
+            unsigned long long kept = 0ull;
+            if (a.keep_all_if_fit && __popcll(live) <= R) {
+                kept = live;
+            } else {
+                // 3. the walk, kWalkB open positions per round
+                unsigned long long open = live;
+                int nk = 0, par = 0;
+                while (open && nk < R) {
+                    int p[kWalkB];
+                    {
+                        unsigned long long rest = open;
+#pragma unroll
+                        for (int b = 0; b < kWalkB; ++b) {
+                            p[b] = rest ? __ffsll((long long)rest) - 1 : -1;
+                            rest &= rest - 1ull;
+                        }
+                    }
+                    // occlusion of this thread's position by each batch member
+                    // before it; a warp with no open position after p[0] skips
+                    const unsigned long long after = open & ~((2ull << p[0]) - 1ull);
+                    const unsigned wopen = (unsigned)(after >> (32 * warp));
+                    bool oc[kWalkB];
+#pragma unroll
+                    for (int b = 0; b < kWalkB; ++b) oc[b] = false;
+                    if (wopen) {
+                        f2_t acc[kWalkB];
+                        const float4 *kr[kWalkB];
+#pragma unroll
+                        for (int b = 0; b < kWalkB; ++b) {
+                            acc[b] = 0ull;
+                            kr[b] = s.rows + (p[b] >= 0 ? p[b] : 0) * kWalkStride;
+                        }
+#pragma unroll
+                        for (int f = 0; f < kWalkMaxF4; ++f) {
+                            if (f < F4) {
+                                const ulonglong2 x = *reinterpret_cast<const ulonglong2 *>(&xr[f]);
+#pragma unroll
+                                for (int b = 0; b < kWalkB; ++b)
+                                    acc[b] = chain2(acc[b], *reinterpret_cast<const ulonglong2 *>(&kr[b][f]), x, kMetric);
+                            }
+                        }
+                        const bool mine_open = (open >> tid) & 1ull;
+#pragma unroll
+                        for (int b = 0; b < kWalkB; ++b)
+                            oc[b] = mine_open && p[b] >= 0 && p[b] < tid &&
+                                    fmaf(a.alpha, chain2_final(acc[b], kMetric), -my_dvc) <= 0.f;
+                    }
+#pragma unroll
+                    for (int b = 0; b < kWalkB; ++b) {
+                        const unsigned m = __ballot_sync(0xffffffffu, oc[b]);
+                        if (lane == 0) s.occ[par][b][warp] = m;
+                    }
+                    __syncthreads();
+                    // resolve the batch in order
+                    unsigned long long drop = 0ull;
+#pragma unroll
+                    for (int b = 0; b < kWalkB; ++b) {
+                        if (p[b] < 0 || nk == R) break;
+                        const unsigned long long bit = 1ull << p[b];
+                        if (drop & bit) continue;   // occluded by a kept member
+                        kept |= bit;
+                        ++nk;
+                        drop |= (unsigned long long)s.occ[par][b][0] |
+                                ((unsigned long long)s.occ[par][b][1] << 32);
+                    }
+                    // everything up to the last member is decided
+                    const int plast = p[kWalkB - 1] >= 0 ? p[kWalkB - 1] : 63;
+                    open &= ~drop & ~((2ull << plast) - 1ull);   // 2 << 63 wraps to 0: all
+                    par ^= 1;
+                }
+            }
+            // 4. output in (distance, id) order: the kept positions
+            if (warp == 0) {
+                const int nk = __popcll(kept);
+                int32_t *out = a.out + (a.out_by_index ? i : (int64_t)owner) * R;
+                const bool k0 = (kept >> lane) & 1ull, k1 = (kept >> (lane + 32)) & 1ull;
+                const int p0 = __popcll(kept & ((1ull << lane) - 1ull));
+                const int p1 = __popcll(kept & ((1ull << (lane + 32)) - 1ull));
+                const int32_t id0 = k0 ? s.sid[lane] : -1, id1 = k1 ? s.sid[lane + 32] : -1;
+                if (k0) out[p0] = id0;
+                if (k1) out[p1] = id1;
+                for (int j = nk + lane; j < R; j += 32) out[j] = -1;
+                if (a.eu) {
+                    const bool e0 = k0 && id0 >= a.emit_lo && id0 < a.emit_hi;
+                    const bool e1 = k1 && id1 >= a.emit_lo && id1 < a.emit_hi;
+                    const unsigned b0 = __ballot_sync(0xffffffffu, e0);
+                    const unsigned b1 = __ballot_sync(0xffffffffu, e1);
+                    const int cnt = __popc(b0) + __popc(b1);
+                    int base = 0;
+                    if (lane == 0 && cnt) base = (int)atomicAdd(a.ecount, (unsigned long long)cnt);
+                    base = __shfl_sync(0xffffffffu, base, 0);
+                    if (e0) {
+                        const int slot = base + __popc(b0 & lanemask_lt());
+                        a.eu[slot] = id0;
+                        a.ev[slot] = owner;
+                    }
+                    if (e1) {
+                        const int slot = base + __popc(b0) + __popc(b1 & lanemask_lt());
+                        a.eu[slot] = id1;
+                        a.ev[slot] = owner;
+                    }
+                }
+            }
+            __syncthreads();   // the owner's shared state is free
+        }
+    }
+}
+
 }  // namespace
 
 // The general FP32 prune (any pool up to 4,096 raw candidates); with idx_list,
@@ -830,6 +1077,29 @@ cudaError_t launch_prune_general(const PruneArgs &a, const int32_t *idx_list,
     }
     kern<<<(unsigned)grid, kThreads, smem, st>>>(a, rows_cap, pool_cap, slow ? 1 : 0, chunk,
                                                  idx_list, idx_count);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_walk(const PruneArgs &a, cudaStream_t st) {
+    static_assert(4 * kWalkMaxF4 == kPruneWalkMaxDim, "rows held in registers");
+    if (a.dim > kPruneWalkMaxDim) return cudaErrorInvalidValue;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(prune_walk_kernel<0>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaFuncSetAttribute(prune_walk_kernel<1>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, prune_walk_kernel<0>, kWalkThreads, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    const int chunk = a.skip_empty_csr ? 32 : 4;
+    int64_t grid = (int64_t)sms * per_sm;
+    const int64_t want = (a.n_owners + chunk - 1) / chunk;
+    if (want < grid) grid = want;
+    if (a.metric == 0)
+        prune_walk_kernel<0><<<(unsigned)grid, kWalkThreads, 0, st>>>(a, chunk);
+    else
+        prune_walk_kernel<1><<<(unsigned)grid, kWalkThreads, 0, st>>>(a, chunk);
     note_launches(1);
     return cudaGetLastError();
 }

@@ -18,8 +18,9 @@ namespace {
 //   kVarTile: the general tensor-core tile (one owner per 128 x 144 tile; BF16
 //             at L2 with the FP32 rows split into two terms, or the library's
 //             stored BF16 / E4M3 terms);
-//   kVarFp32: the FP32 kernels (register-blocked triangle for pools <= 64).
-enum { kVarFp32 = 0, kVarPair = 1, kVarTile = 2, kVarCount = 3 };
+//   kVarFp32: the FP32 kernels (register-blocked triangle for pools <= 64);
+//   kVarWalk: the FP32 walk over kept rows (pools <= 64, d <= 128).
+enum { kVarFp32 = 0, kVarPair = 1, kVarTile = 2, kVarWalk = 3, kVarCount = 4 };
 
 // The variant, as launch_prune always ran it: pair tile, else tile, else FP32.
 cudaError_t run_variant(const PruneArgs &a, int var, cudaStream_t st) {
@@ -36,7 +37,10 @@ cudaError_t run_variant(const PruneArgs &a, int var, cudaStream_t st) {
     if (!small_ok) return launch_prune_general(a, nullptr, nullptr, st);
     cudaError_t e = cudaMemsetAsync(a.ovf_count, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
-    e = pair ? launch_prune_pair(a, st) : tc ? launch_prune_tc(a, st, terms) : launch_small(a, st);
+    e = pair ? launch_prune_pair(a, st)
+        : tc ? launch_prune_tc(a, st, terms)
+        : var == kVarWalk ? launch_walk(a, st)
+        : launch_small(a, st);
     if (e != cudaSuccess) return e;
     if (a.lenA + a.lenB + (a.csr_offs ? a.csr_max : 0) <= cap) return cudaSuccess;
     // owners whose pools exceeded the first kernel (the count stays on the device)
@@ -59,6 +63,7 @@ int variants_of(const PruneArgs &a, int *out) {
             a.lenA + a.lenB <= prune_tc_max_pool())
             out[n++] = kVarTile;
     }
+    if (a.dim <= kPruneWalkMaxDim) out[n++] = kVarWalk;
     out[n++] = kVarFp32;
     return n;
 }
@@ -106,16 +111,19 @@ int forced_prune_variant() {
 
 }  // namespace
 
-cudaError_t launch_prune(const PruneArgs &a, cudaStream_t st) {
+cudaError_t launch_prune(const PruneArgs &a, cudaStream_t st, int *variant) {
+    int dummy = -1;
+    int &ran = variant ? *variant : dummy;
     if (a.n_owners <= 0) return cudaSuccess;
     if (a.R > 64 || a.dim > 1024 || (a.dim & 3)) return cudaErrorInvalidValue;
     int vars[kVarCount];
     const int nv = variants_of(a, vars);
     auto run = [&](const PruneArgs &x, int v) {
-        if (v == kVarFp32 && x.prec != 0) {
+        ran = v;
+        if ((v == kVarFp32 || v == kVarWalk) && x.prec != 0) {
             PruneArgs y = x;
             y.prec = 0;
-            return run_variant(y, kVarFp32, st);
+            return run_variant(y, v, st);
         }
         return run_variant(x, v, st);
     };
@@ -168,6 +176,7 @@ cudaError_t launch_prune(const PruneArgs &a, cudaStream_t st) {
         if (ms_of[vars[k]] * own_of[best] < ms_of[best] * own_of[vars[k]]) best = vars[k];
     std::lock_guard<std::mutex> lk(g_ptune_mu);
     g_ptuned[key] = best;
+    ran = best;
     return cudaSuccess;
 }
 

@@ -57,7 +57,7 @@ class Stats(C.Structure):
                 ("launches", C.c_int64), ("phase_ms", C.c_double * 8),
                 ("search_ndc", C.c_int64 * 3), ("search_exp", C.c_int64 * 3),
                 ("search_queries", C.c_int64 * 3), ("tile_error", C.c_double * 4),
-                ("tile_tests", C.c_int64)]
+                ("tile_tests", C.c_int64), ("prune_kernel", C.c_int32 * 2)]
 
     def as_dict(self):
         out = {}

@@ -524,7 +524,7 @@ def test_prune_variants_and_autotuned_choice_agree(rn, monkeypatch, kind):
     if kind == "sift":   # integer rows: exact against the oracle
         np.testing.assert_array_equal(ref[:2000], want)
     for prec in (rn.BF16, rn.FP8):
-        for force in ("1", "2", "0", None):
+        for force in ("1", "2", "0", "3", None):
             if force is None:
                 monkeypatch.delenv("RNSM_PRUNE_VARIANT", raising=False)
             else:
