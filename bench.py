@@ -857,7 +857,27 @@ def measure_extra(W, rn, torch, steps, warm, nq, scale=1.0, curves=False):
          "plan_edges": len(rn.mos_plan(sizes, cen)),
          "steps": steps, "warmup": warm, "input_graph_build_s": round(build_s, 3),
          "fp32": {"ms_per_step": ms32, "value": N / (ms32 / 1000.0), "unit": UNIT,
-                  "phase_ms": [round(x, 3) for x in st32["phase_ms"]]}}
+                  "phase_ms": [round(x, 3) for x in st32["phase_ms"]],
+                  "prune_kernel_s6_s7": list(st32["prune_kernel"])}}
+    if curves:
+        # the batching pattern's effect: the same merge with one search launch per
+        # plan edge (RNSM_SEARCH_PER_JOB=1) instead of one launch per phase over
+        # every edge of the plan; same queries, same graph
+        oj = torch.empty_like(out)
+        os.environ["RNSM_SEARCH_PER_JOB"] = "1"
+        try:
+            msj, stj = timed(rn.params(W.R, W.L, W.alpha, metric=W.metric), oj)
+        finally:
+            del os.environ["RNSM_SEARCH_PER_JOB"]
+        srch = lambda st: round(st["phase_ms"][1] + st["phase_ms"][4] + st["phase_ms"][5], 3)
+        r["batching"] = {"one_launch_per_phase_ms_per_step": ms32,
+                         "one_launch_per_edge_ms_per_step": msj,
+                         "search_ms_one_launch_per_phase": srch(st32),
+                         "search_ms_one_launch_per_edge": srch(stj),
+                         "launches_one_per_phase": int(st32["launches"]),
+                         "launches_one_per_edge": int(stj["launches"]),
+                         "identical": bool(torch.equal(oj, out))}
+        del oj
     oq = torch.empty_like(out)
     for name in W.modes:
         prec = {"bf16": rn.BF16, "fp8": rn.FP8}[name]

@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -288,6 +289,22 @@ rnsm_status run_search(SearchArgs a, int32_t *work, cudaStream_t st) {
     CK(cudaMemsetAsync(work, 0, sizeof(int32_t), st));
     a.work = work;
     CK(launch_search(a, st));
+    return RNSM_OK;
+}
+
+// A multi-job search as one launch per job (RNSM_SEARCH_PER_JOB=1: the same
+// queries and results, for measuring what one launch over every job gains);
+// hj: the host copy of the job table, its sentinel included.
+rnsm_status run_search_jobs(const SearchArgs &a, int32_t *work, const std::vector<SearchJob> &hj,
+                            cudaStream_t st) {
+    const char *f = getenv("RNSM_SEARCH_PER_JOB");
+    if (!(f && f[0] == '1') || hj.size() < 3) return run_search(a, work, st);
+    for (size_t k = 0; k + 1 < hj.size(); ++k) {
+        SearchArgs b = a;
+        b.q0 = hj[k].q_begin;
+        b.nq = hj[k + 1].q_begin - hj[k].q_begin;
+        if (b.nq > 0) TRY(run_search(b, work, st));
+    }
     return RNSM_OK;
 }
 
@@ -1128,7 +1145,7 @@ rnsm_status rnsm_merge(const rnsm_segment *segs, int32_t m, const rnsm_params *p
         a.stats = c.stats;
         a.jobs = mb.jobs1;
         a.n_jobs = (int32_t)srcs.size();
-        TRY(run_search(a, c.work, st));
+        TRY(run_search_jobs(a, c.work, jobs, st));
         queries[0] += total;
         tm.end(t1);
         // S2 (reverse kNN inversion) and S3 (pivots) per source
@@ -1223,6 +1240,7 @@ rnsm_status rnsm_merge(const rnsm_segment *segs, int32_t m, const rnsm_params *p
     // enqueues S4, S5 and the per-edge S6 / S7 of a group; no host synchronisation
     // when `graph` (the reverse pools are then sized by their static bound)
     auto enqueue_group = [&](size_t gi, bool graph, int64_t tot4, int64_t tot5,
+                             const std::vector<SearchJob> &hj4, const std::vector<SearchJob> &hj5,
                              cudaStream_t es) -> rnsm_status {
         const size_t g0 = groups[gi].first, g1 = groups[gi].second;
         int span = graph ? -1 : tm.begin(4);
@@ -1239,7 +1257,7 @@ rnsm_status rnsm_merge(const rnsm_segment *segs, int32_t m, const rnsm_params *p
             a.stats = c.stats + 2;
             a.jobs = mb.jobs4;
             a.n_jobs = (int32_t)(g1 - g0);
-            TRY(run_search(a, c.work, es));
+            TRY(run_search_jobs(a, c.work, hj4, es));
         }
         tm.end(span);
         span = graph ? -1 : tm.begin(5);
@@ -1258,7 +1276,7 @@ rnsm_status rnsm_merge(const rnsm_segment *segs, int32_t m, const rnsm_params *p
             a.stats = c.stats + 4;
             a.jobs = mb.jobs5;
             a.n_jobs = (int32_t)(g1 - g0);
-            TRY(run_search(a, c.work + 3, es));
+            TRY(run_search_jobs(a, c.work + 3, hj5, es));
         }
         tm.end(span);
         if (uni) {
@@ -1371,7 +1389,7 @@ rnsm_status rnsm_merge(const rnsm_segment *segs, int32_t m, const rnsm_params *p
         queries[1] += tot4;
         queries[2] += tot5;
         if (!want_graph) {
-            TRY(enqueue_group(gi, false, tot4, tot5, st));
+            TRY(enqueue_group(gi, false, tot4, tot5, j4, j5, st));
             continue;
         }
         // graph mode: capture once, replay while the key matches
@@ -1385,7 +1403,7 @@ rnsm_status rnsm_merge(const rnsm_segment *segs, int32_t m, const rnsm_params *p
             // captured); the graph is launched on the caller's stream below
             if (!gc.stream) CK(cudaStreamCreateWithFlags(&gc.stream, cudaStreamNonBlocking));
             CK(cudaStreamBeginCapture(gc.stream, cudaStreamCaptureModeRelaxed));
-            const rnsm_status rs = enqueue_group(gi, true, tot4, tot5, gc.stream);
+            const rnsm_status rs = enqueue_group(gi, true, tot4, tot5, j4, j5, gc.stream);
             cudaGraph_t graph = nullptr;
             const cudaError_t ce = cudaStreamEndCapture(gc.stream, &graph);
             if (rs != RNSM_OK) {

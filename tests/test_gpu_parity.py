@@ -277,12 +277,15 @@ def test_merge_tiny_segments_exact(rn):
         np.testing.assert_array_equal(host(got), want)
 
 
-@pytest.mark.parametrize("flags", [0, 2])
-def test_merge_batched_plan_with_shared_sources_exact(rn, flags):
+@pytest.mark.parametrize("flags,per_job", [(0, False), (2, False), (0, True)])
+def test_merge_batched_plan_with_shared_sources_exact(rn, monkeypatch, flags, per_job):
     # six uneven segments, a hand-made plan where sources serve several edges and
     # segments are source and target in turn: the batched executor (all S1 in
     # one launch, all S4 and all S5 of the plan in one launch each) must give
-    # Algorithm 2 applied edge by edge
+    # Algorithm 2 applied edge by edge; so must one search launch per plan edge
+    # (RNSM_SEARCH_PER_JOB=1, the batching measurement's comparison)
+    if per_job:
+        monkeypatch.setenv("RNSM_SEARCH_PER_JOB", "1")
     sizes = [700, 1300, 450, 1000, 820, 1600]
     segs = [gen.sift_like(n, 60 + i, d=64) for i, n in enumerate(sizes)]
     gs = [oracle.build_graph(s, 16, 32, 1.2) for s in segs]
