@@ -321,6 +321,7 @@ rnsm_status run_prune(PruneArgs a, int32_t *work, const Ctl &c, cudaStream_t st,
     a.work2 = work + 1;
     a.ovf_list = c.ovf;
     a.ovf_count = c.ovf_count;
+    a.tune_site = slot >= 0 && c.kernel_ran ? slot + 1 : 0;   // a merge's S6 / S7, else any
     int ran = -1;
     CK(launch_prune(a, st, &ran));
     if (slot >= 0 && c.kernel_ran) c.kernel_ran[slot] = ran;

@@ -116,6 +116,8 @@ struct PruneArgs {
     const float *qnorm;       // row norms ||x||
     unsigned long long *rechecks;  // decisions re-decided in FP32
     unsigned long long *tile_tests;  // nullable: occlusion tests the tensor-core tiles evaluated
+    int32_t tune_site;       // the prune autotuner's call site (0 any, 1 merge S6, 2 merge S7):
+                             // pools of one shape differ between a graph build and a merge
     unsigned int *tile_err;   // nullable [4]: sampled tile error maxima (float bits) and count
     int32_t *work;
     int32_t *work2;           // second zeroed counter (overflow pass)

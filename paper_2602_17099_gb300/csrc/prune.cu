@@ -816,16 +816,19 @@ __global__ void __launch_bounds__(kSmallThreads, RNSM_SMALL_MIN_BLOCKS) prune_sm
 // triangle kernel (a pair's order does not change it), so the kept lists
 // are identical.
 constexpr int kWalkThreads = 64;
-constexpr int kWalkMaxF4 = 32;   // float4 of a row held in registers (dim <= 128)
-constexpr int kWalkStride = kWalkMaxF4 + 1;   // row stride in float4: 8 rows on 32 banks
+// kF4: float4 of a row held in registers (16, 24 or 32: d <= 64, 96, 128); the
+// row stride in shared memory is kF4 + 1 float4, so 8 rows fall on 32 banks
+template <int kF4>
+constexpr int walk_min_blocks() { return kF4 <= 16 ? 8 : kF4 <= 24 ? 6 : 5; }
 #ifndef RNSM_WALK_B
 #define RNSM_WALK_B 4
 #endif
 constexpr int kWalkB = RNSM_WALK_B;
 
+template <int kF4>
 struct WalkSmem {
-    float4 rows[kSmallMax * kWalkStride];   // candidate rows in position order
-    float4 vrow[kWalkMaxF4];                // the owner's row
+    float4 rows[kSmallMax * (kF4 + 1)];     // candidate rows in position order
+    float4 vrow[kF4];                       // the owner's row
     float kd[kSmallMax];                    // raw keys
     int32_t kix[kSmallMax];
     int32_t sid[kSmallMax];                 // ids in position order
@@ -834,9 +837,11 @@ struct WalkSmem {
     int64_t claim;
 };
 
-template <int kMetric>
-__global__ void __launch_bounds__(kWalkThreads, 5) prune_walk_kernel(const PruneArgs a, int chunk) {
-    __shared__ __align__(16) WalkSmem s;
+template <int kMetric, int kF4>
+__global__ void __launch_bounds__(kWalkThreads, walk_min_blocks<kF4>())
+    prune_walk_kernel(const PruneArgs a, int chunk) {
+    constexpr int kWalkMaxF4 = kF4, kWalkStride = kF4 + 1;
+    __shared__ __align__(16) WalkSmem<kF4> s;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int dim = a.dim, F4 = dim >> 2;
     const int R = a.R;
@@ -1081,27 +1086,40 @@ cudaError_t launch_prune_general(const PruneArgs &a, const int32_t *idx_list,
     return cudaGetLastError();
 }
 
-cudaError_t launch_walk(const PruneArgs &a, cudaStream_t st) {
-    static_assert(4 * kWalkMaxF4 == kPruneWalkMaxDim, "rows held in registers");
-    if (a.dim > kPruneWalkMaxDim) return cudaErrorInvalidValue;
+namespace {
+
+template <int kMetric, int kF4>
+cudaError_t launch_walk_t(const PruneArgs &a, cudaStream_t st) {
+    auto kern = prune_walk_kernel<kMetric, kF4>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaFuncSetAttribute(prune_walk_kernel<0>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    cudaFuncSetAttribute(prune_walk_kernel<1>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, prune_walk_kernel<0>, kWalkThreads, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWalkThreads, 0);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
-    const int chunk = a.skip_empty_csr ? 32 : 4;
+    const int chunk = a.skip_empty_csr ? 8 : 4;
     int64_t grid = (int64_t)sms * per_sm;
     const int64_t want = (a.n_owners + chunk - 1) / chunk;
     if (want < grid) grid = want;
-    if (a.metric == 0)
-        prune_walk_kernel<0><<<(unsigned)grid, kWalkThreads, 0, st>>>(a, chunk);
-    else
-        prune_walk_kernel<1><<<(unsigned)grid, kWalkThreads, 0, st>>>(a, chunk);
+    kern<<<(unsigned)grid, kWalkThreads, 0, st>>>(a, chunk);
     note_launches(1);
     return cudaGetLastError();
+}
+
+template <int kMetric>
+cudaError_t launch_walk_m(const PruneArgs &a, cudaStream_t st) {
+    if (a.dim <= 64) return launch_walk_t<kMetric, 16>(a, st);
+    if (a.dim <= 96) return launch_walk_t<kMetric, 24>(a, st);
+    return launch_walk_t<kMetric, 32>(a, st);
+}
+
+}  // namespace
+
+cudaError_t launch_walk(const PruneArgs &a, cudaStream_t st) {
+    static_assert(4 * 32 == kPruneWalkMaxDim, "rows held in registers");
+    if (a.dim > kPruneWalkMaxDim) return cudaErrorInvalidValue;
+    return a.metric == 0 ? launch_walk_m<0>(a, st) : launch_walk_m<1>(a, st);
 }
 
 cudaError_t launch_small(const PruneArgs &a, cudaStream_t st) {
@@ -1114,7 +1132,7 @@ cudaError_t launch_small(const PruneArgs &a, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     // owners are claimed a few at a time: one atomic round trip per claim
-    const int chunk = a.skip_empty_csr ? 32 : 4;
+    const int chunk = a.skip_empty_csr ? 8 : 4;
     int64_t grid = (int64_t)sms * per_sm;
     const int64_t want = (a.n_owners + chunk - 1) / chunk;
     if (want < grid) grid = want;

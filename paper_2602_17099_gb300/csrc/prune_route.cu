@@ -1,5 +1,6 @@
 // Routing of a prune call to its kernels, and the autotuner over the prune
 // variants (tensor-core tile shapes and the FP32 kernels); host code only.
+#include <stdio.h>
 #include <stdlib.h>
 
 #include <map>
@@ -80,20 +81,24 @@ PruneArgs owner_slice(const PruneArgs &a, int64_t o0, int64_t o1) {
     return b;
 }
 
-// Autotuner over the variants: the first call of a shape (precision,
-// dimension, metric, pool length, reverse-edge pools or not) with at least
+// Autotuner over the variants: the first call of a shape (call site,
+// precision, dimension, metric, pool length, reverse-edge pools or not) with at least
 // kPruneTuneChunks * kPruneTuneMinChunk owners runs as kPruneTuneChunks
 // consecutive slices of its owners, the variants taking turns (the order
 // rotating every round), each slice timed with CUDA events on the launching
 // stream; the variant with the least time per owner is kept for the process.
 // A variant's first slice is left out of its time (it may pay the lazy load
 // of its kernel's module).  Every owner is pruned once.  Not while the stream
-// is being captured.
+// is being captured, and for reverse-edge pools only on a call with at least
+// kPruneTuneMinEntries incoming entries.  RNSM_TUNE_LOG=1 prints each choice
+// and its times to stderr, =2 every slice too.
 constexpr int kPruneTuneChunks = 12;
 constexpr int64_t kPruneTuneMinChunk = 5000;
+constexpr int64_t kPruneTuneMinEntries = 100000;   // reverse-edge pools: incoming entries
 struct PruneKey {
-    int prec, dim, metric, len, csr;
+    int prec, dim, metric, len, csr, site;
     bool operator<(const PruneKey &o) const {
+        if (site != o.site) return site < o.site;
         if (prec != o.prec) return prec < o.prec;
         if (dim != o.dim) return dim < o.dim;
         if (metric != o.metric) return metric < o.metric;
@@ -132,7 +137,7 @@ cudaError_t launch_prune(const PruneArgs &a, cudaStream_t st, int *variant) {
         for (int k = 0; k < nv; ++k)
             if (vars[k] == forced) return run(a, forced);
     if (nv == 1) return run(a, vars[0]);
-    const PruneKey key{a.prec, a.dim, a.metric, a.lenA + a.lenB, a.csr_offs != nullptr};
+    const PruneKey key{a.prec, a.dim, a.metric, a.lenA + a.lenB, a.csr_offs != nullptr, a.tune_site};
     {
         std::lock_guard<std::mutex> lk(g_ptune_mu);
         auto it = g_ptuned.find(key);
@@ -142,6 +147,17 @@ cudaError_t launch_prune(const PruneArgs &a, cudaStream_t st, int *variant) {
     if (a.n_owners < kPruneTuneChunks * kPruneTuneMinChunk || !a.work || !a.work2 ||
         cudaStreamIsCapturing(st, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone)
         return run(a, vars[0]);
+    if (a.csr_offs) {
+        // reverse-edge pools: most owners of an early call may have no entries
+        // (the first batches of a graph build); tune only on a call with work
+        int64_t ends[2] = {0, 0};
+        if (cudaMemcpyAsync(&ends[0], a.csr_offs, sizeof(int64_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaMemcpyAsync(&ends[1], a.csr_offs + a.n_owners, sizeof(int64_t), cudaMemcpyDeviceToHost, st) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return run(a, vars[0]);
+        if (ends[1] - ends[0] < kPruneTuneMinEntries) return run(a, vars[0]);
+    }
     double ms_of[kVarCount] = {}, own_of[kVarCount] = {};
     bool seen[kVarCount] = {};
     cudaEvent_t e0, e1;
@@ -167,6 +183,10 @@ cudaError_t launch_prune(const PruneArgs &a, cudaStream_t st, int *variant) {
             own_of[v] += (double)(o1 - o0);
         }
         seen[v] = true;
+        const char *lg = getenv("RNSM_TUNE_LOG");
+        if (lg && lg[0] == '2')
+            fprintf(stderr, "rnsm prune tuner: slice %d variant %d owners %lld..%lld %.3f ms\n", c, v,
+                    (long long)o0, (long long)o1, ms);
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -174,6 +194,14 @@ cudaError_t launch_prune(const PruneArgs &a, cudaStream_t st, int *variant) {
     int best = vars[0];
     for (int k = 1; k < nv; ++k)
         if (ms_of[vars[k]] * own_of[best] < ms_of[best] * own_of[vars[k]]) best = vars[k];
+    const char *lg = getenv("RNSM_TUNE_LOG");
+    if (lg && (lg[0] == '1' || lg[0] == '2')) {
+        fprintf(stderr, "rnsm prune tuner: site %d prec %d dim %d metric %d len %d csr %d owners %lld:",
+                key.site, key.prec, key.dim, key.metric, key.len, key.csr, (long long)a.n_owners);
+        for (int k = 0; k < nv; ++k)
+            fprintf(stderr, " variant %d %.3f ms / %.0f owners;", vars[k], ms_of[vars[k]], own_of[vars[k]]);
+        fprintf(stderr, " chose %d\n", best);
+    }
     std::lock_guard<std::mutex> lk(g_ptune_mu);
     g_ptuned[key] = best;
     ran = best;
