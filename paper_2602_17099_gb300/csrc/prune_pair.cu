@@ -864,7 +864,9 @@ cudaError_t launch_prune_pair(const PruneArgs &in, cudaStream_t st) {
     if (by_regs < per_sm) per_sm = by_regs;
     if (per_sm > 512 / kQCols) per_sm = 512 / kQCols;
     if (per_sm < 1) per_sm = 1;
-    const int chunk = a.skip_empty_csr ? 64 : 8;
+    // owners per claim: reverse-edge pools skip their empty owners, so they claim more,
+    // but not so many that the last claims leave a tail (32: about 12 pairs)
+    const int chunk = a.skip_empty_csr ? 32 : 8;
     int64_t grid = (int64_t)sms * per_sm;
     const int64_t want = (a.n_owners + chunk - 1) / chunk;
     if (want < grid) grid = want;

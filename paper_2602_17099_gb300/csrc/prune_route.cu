@@ -64,8 +64,15 @@ int variants_of(const PruneArgs &a, int *out) {
             a.lenA + a.lenB <= prune_tc_max_pool())
             out[n++] = kVarTile;
     }
-    if (a.dim <= kPruneWalkMaxDim) out[n++] = kVarWalk;
-    out[n++] = kVarFp32;
+    // FP32 defaults (calls too small to tune): the walk for the source pools, the
+    // triangle for reverse-edge pools (on deep-like rows the walk lost there by 40 %)
+    if (a.csr_offs) {
+        out[n++] = kVarFp32;
+        if (a.dim <= kPruneWalkMaxDim) out[n++] = kVarWalk;
+    } else {
+        if (a.dim <= kPruneWalkMaxDim) out[n++] = kVarWalk;
+        out[n++] = kVarFp32;
+    }
     return n;
 }
 
@@ -93,7 +100,7 @@ PruneArgs owner_slice(const PruneArgs &a, int64_t o0, int64_t o1) {
 // kPruneTuneMinEntries incoming entries.  RNSM_TUNE_LOG=1 prints each choice
 // and its times to stderr, =2 every slice too.
 constexpr int kPruneTuneChunks = 12;
-constexpr int64_t kPruneTuneMinChunk = 5000;
+constexpr int64_t kPruneTuneMinChunk = 20000;   // owners per slice: short launches are tail-bound
 constexpr int64_t kPruneTuneMinEntries = 100000;   // reverse-edge pools: incoming entries
 struct PruneKey {
     int prec, dim, metric, len, csr, site;

@@ -515,12 +515,12 @@ def test_expand_autotuned_on_large_batch(rn):
 
 @pytest.mark.parametrize("kind", ["sift", "deepl2"])
 def test_prune_variants_and_autotuned_choice_agree(rn, monkeypatch, kind):
-    # the prune variants (pair tile, general tile, FP32 kernels) take the FP32
-    # decisions; 70,000 owners trigger the autotuner (slices of the owners run
-    # with each variant in turn), whose choice must not change the result
-    n = 80000
+    # the prune variants (pair tile, general tile, FP32 walk and triangle) take the
+    # FP32 decisions; 250,000 owners trigger the autotuner (slices of the owners
+    # run with each variant in turn), whose choice must not change the result
+    n = 260000
     X = gen.sift_like(n, 111, d=128) if kind == "sift" else gen.deep_like(n, 112, d=96)
-    owners, pool = _pools(n, 64, 113, 70000)
+    owners, pool = _pools(n, 64, 113, 250000)
     Xd, od, pd_ = dev(X), dev(owners), dev(pool)
     ref = host(rn.prune(Xd, od, pd_, 32, 1.2))
     want, _ = oracle.prune(X, owners[:2000].astype(np.int64), pool[:2000], 32, 1.2)
