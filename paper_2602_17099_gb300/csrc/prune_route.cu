@@ -23,7 +23,8 @@ namespace {
 //   kVarWalk: the FP32 walk over kept rows (pools <= 64, d <= 128).
 enum { kVarFp32 = 0, kVarPair = 1, kVarTile = 2, kVarWalk = 3, kVarCount = 4 };
 
-// The variant, as launch_prune always ran it: pair tile, else tile, else FP32.
+// One variant over a call's owners: its kernel for the pools it takes, the
+// general FP32 kernel for the owners whose pools exceed that kernel's capacity.
 cudaError_t run_variant(const PruneArgs &a, int var, cudaStream_t st) {
     const bool pair_ok = a.prec != 0 && prune_pair_ok(a.dim, a.prec, a.metric);
     const bool pair = var == kVarPair;
@@ -66,11 +67,12 @@ int variants_of(const PruneArgs &a, int *out) {
     }
     // FP32 defaults (calls too small to tune): the walk for the source pools, the
     // triangle for reverse-edge pools (on deep-like rows the walk lost there by 40 %)
+    const bool walk_ok = a.dim <= kPruneWalkMaxDim && a.lenA + a.lenB <= kPruneSmallMax;
     if (a.csr_offs) {
         out[n++] = kVarFp32;
-        if (a.dim <= kPruneWalkMaxDim) out[n++] = kVarWalk;
+        if (walk_ok) out[n++] = kVarWalk;
     } else {
-        if (a.dim <= kPruneWalkMaxDim) out[n++] = kVarWalk;
+        if (walk_ok) out[n++] = kVarWalk;
         out[n++] = kVarFp32;
     }
     return n;
