@@ -29,6 +29,21 @@
  *   RNSM_EINVAL, out-of-range vertex ids or non-finite vectors RNSM_EGRAPH.
  *   CUDA failures give RNSM_ECUDA.  rnsm_last_error() describes the last
  *   non-OK status of the calling thread.
+ * - Autotuning: the first large search launch of a shape and the first large
+ *   prune call of a shape time their kernel variants on slices of the call and
+ *   keep the fastest for the process; every variant gives the same results.
+ *   Environment variables read at each call (none changes a result):
+ *     RNSM_SEARCH_VARIANT=v   force search launch variant v (0..3)
+ *     RNSM_PRUNE_VARIANT=v    force prune variant v where it applies (0 the
+ *                             FP32 triangle, 1 the pair tile, 2 the general
+ *                             tile, 3 the FP32 walk)
+ *     RNSM_TUNE_LOG=1|2       print the prune tuner's choices (2: and slices)
+ *                             to stderr
+ *     RNSM_SEARCH_PER_JOB=1   run a plan's multi-job searches as one launch
+ *                             per plan edge (to measure the batched launches)
+ *     RNSM_TEST_WITHHOLD_COMMIT  tests only: the tensor-core prune withholds
+ *                             its MMA completion signal, so that its bounded
+ *                             wait runs out (RNSM_ETIMEOUT)
  */
 #ifndef RNSM_H_
 #define RNSM_H_
