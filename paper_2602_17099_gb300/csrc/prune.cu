@@ -824,6 +824,9 @@ constexpr int walk_min_blocks() { return kF4 <= 16 ? 8 : kF4 <= 24 ? 6 : 5; }
 #define RNSM_WALK_B 4
 #endif
 constexpr int kWalkB = RNSM_WALK_B;
+#ifndef RNSM_WALK_CHUNK
+#define RNSM_WALK_CHUNK 4   // source-pool owners per claim (4: 13.30 ms, 8: 13.35, 16: 13.44 on S6)
+#endif
 
 template <int kF4>
 struct WalkSmem {
@@ -845,6 +848,11 @@ __global__ void __launch_bounds__(kWalkThreads, walk_min_blocks<kF4>())
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int dim = a.dim, F4 = dim >> 2;
     const int R = a.R;
+    // this thread's candidate row; the next owner's is loaded into it at the end
+    // of an owner's walk, so its latency overlaps the output and the claim
+    float4 xr[kWalkMaxF4];
+    int64_t pre_i = -1;     // owner index whose candidate row xr already holds
+    int32_t pre_id = -1;    // that candidate's id
     for (;;) {
         if (tid == 0) s.claim = atomicAdd(a.work, chunk);
         __syncthreads();
@@ -869,7 +877,10 @@ __global__ void __launch_bounds__(kWalkThreads, walk_min_blocks<kF4>())
             // 1. raw candidate tid: its row into registers, the owner's row to
             //    shared memory, the candidate's key (d(v,c), id)
             int32_t id = -1;
-            if (tid < nr) {
+            const bool have = pre_i == i;
+            if (have) {
+                id = pre_id;
+            } else if (tid < nr) {
                 if (tid < a.lenA) {
                     id = a.listA[(int64_t)owner * a.lenA + tid];
                 } else if (tid < a.lenA + a.lenB) {
@@ -882,8 +893,7 @@ __global__ void __launch_bounds__(kWalkThreads, walk_min_blocks<kF4>())
             }
             const float *orow = seg_row(a.segs, owner, dim);
             if (tid < F4) s.vrow[tid] = ldg4(orow + 4 * tid);
-            float4 xr[kWalkMaxF4];
-            {
+            if (!have) {
                 const float *row = seg_row(a.segs, id >= 0 ? id : owner, dim);
 #pragma unroll
                 for (int f = 0; f < kWalkMaxF4; ++f)
@@ -1011,6 +1021,39 @@ __global__ void __launch_bounds__(kWalkThreads, walk_min_blocks<kF4>())
                     par ^= 1;
                 }
             }
+            // the next owner of the claim: its candidate's row into xr now (the
+            // walk is done with it); the same ids and rows as its own phase 1 loads
+            pre_i = -1;
+            if (i + 1 < i1) {
+                const int64_t in = i + 1;
+                const int32_t on = a.owner_ids ? a.owner_ids[in] : (int32_t)(a.owner_base + in);
+                int64_t cl = 0, ch = 0;
+                if (a.csr_offs) {
+                    cl = a.csr_offs[in];
+                    ch = a.csr_offs[in + 1];
+                }
+                const int64_t nrn = (int64_t)a.lenA + a.lenB + (ch - cl);
+                if (!(a.skip_empty_csr && ch == cl) && nrn <= kSmallMax) {
+                    int32_t idn = -1;
+                    if (tid < nrn) {
+                        if (tid < a.lenA) {
+                            idn = a.listA[(int64_t)on * a.lenA + tid];
+                        } else if (tid < a.lenA + a.lenB) {
+                            idn = a.listB[in * a.strideB + (tid - a.lenA)];
+                            if (idn >= 0) idn += a.offB;
+                        } else {
+                            idn = a.csr_ids[cl + (tid - a.lenA - a.lenB)];
+                        }
+                        if (idn == on) idn = -1;
+                    }
+                    const float *row = seg_row(a.segs, idn >= 0 ? idn : on, dim);
+#pragma unroll
+                    for (int f = 0; f < kWalkMaxF4; ++f)
+                        if (f < F4) xr[f] = ldg4(row + 4 * f);
+                    pre_i = in;
+                    pre_id = idn;
+                }
+            }
             // 4. output in (distance, id) order: the kept positions
             if (warp == 0) {
                 const int nk = __popcll(kept);
@@ -1098,7 +1141,9 @@ cudaError_t launch_walk_t(const PruneArgs &a, cudaStream_t st) {
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWalkThreads, 0);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
-    const int chunk = a.skip_empty_csr ? 8 : 4;
+    // owners per claim: the next owner's rows are loaded during the current one's
+    // walk only within a claim
+    const int chunk = a.skip_empty_csr ? 8 : RNSM_WALK_CHUNK;
     int64_t grid = (int64_t)sms * per_sm;
     const int64_t want = (a.n_owners + chunk - 1) / chunk;
     if (want < grid) grid = want;
