@@ -173,7 +173,8 @@ typedef struct {
     /* The prune kernel that served the last S6 call and the last S7 pool prune
      * (the autotuner's choice): 0 the FP32 register-blocked triangle, 1 the
      * pair tensor-core tile, 2 the general tensor-core tile, 3 the FP32 walk
-     * over kept rows; -1 none ran. */
+     * over kept rows; -1 none ran, or the call replayed a captured CUDA graph
+     * (RNSM_FLAG_GRAPH), whose kernels were chosen when it was captured. */
     int32_t prune_kernel[2];
 } rnsm_stats;
 
